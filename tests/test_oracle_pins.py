@@ -1,0 +1,355 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+exact identities on integer data, invariants, special cases that reduce to numpy,
+and the numbers the paper prints (tests/golden/).  None of them needs a GPU.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_00709_gb300 import inputs
+
+CLAMP, PERIODIC, ZERO = 0, 1, 2
+
+
+def seven(cc, cw, ce, cn, cs, cb, ct):
+    return [(0, 0, 0, cc), (-1, 0, 0, cw), (1, 0, 0, ce), (0, -1, 0, cn), (0, 1, 0, cs),
+            (0, 0, -1, cb), (0, 0, 1, ct)]
+
+
+def int_grid(shape, seed, hi=1 << 10):
+    nx, ny, nz = shape
+    return np.random.default_rng(seed).integers(0, hi, size=(nz, ny, nx)).astype(np.float64)
+
+
+# ----------------------------------------------------------- Eq. (1): sweep
+
+@pytest.mark.parametrize("boundary", [CLAMP, PERIODIC, ZERO])
+def test_sweep_identity_stencil(orc, boundary):
+    shape = (7, 5, 3)
+    u = np.random.default_rng(0).normal(size=shape[::-1])
+    st = orc.Stencil(shape, [(0, 0, 0, 1.0)], boundary)
+    np.testing.assert_array_equal(orc.sweep(st, np.zeros_like(u), u), u)
+
+
+def test_sweep_constant_term_only(orc):
+    shape = (6, 4, 3)
+    C = np.random.default_rng(1).normal(size=shape[::-1])
+    st = orc.Stencil(shape, seven(0.5, .1, .1, .1, .1, .05, .05))
+    np.testing.assert_array_equal(orc.sweep(st, C, np.zeros_like(C)), C)
+
+
+def test_sweep_impulse_response(orc):
+    """out[p] = sum_d w_d u[p+d]; a unit impulse at q lands weight w_d at q - d.
+    Seven distinct dyadic weights pin the direction of every offset and the axis order."""
+    shape = (9, 8, 7)
+    w = dict(cc=1 / 2, cw=1 / 4, ce=1 / 8, cn=1 / 16, cs=1 / 32, cb=1 / 64, ct=1 / 128)
+    st = orc.Stencil(shape, seven(**w))
+    u = np.zeros(shape[::-1])
+    q = (3, 4, 5)  # (z, y, x)
+    u[q] = 1.0
+    out = orc.sweep(st, np.zeros_like(u), u)
+    expect = np.zeros_like(u)
+    z, y, x = q
+    expect[z, y, x] = w["cc"]
+    expect[z, y, x + 1] = w["cw"]   # west neighbour of x+1 is x
+    expect[z, y, x - 1] = w["ce"]
+    expect[z, y + 1, x] = w["cn"]   # north = y-1 (Fig. 2: n = c - nx)
+    expect[z, y - 1, x] = w["cs"]
+    expect[z + 1, y, x] = w["cb"]
+    expect[z - 1, y, x] = w["ct"]
+    np.testing.assert_array_equal(out, expect)
+
+
+def test_sweep_clamped_corner(orc):
+    """Fig. 2: a neighbour outside the grid is replaced by the centre."""
+    shape = (5, 6, 4)
+    w = dict(cc=1 / 2, cw=1 / 4, ce=1 / 8, cn=1 / 16, cs=1 / 32, cb=1 / 64, ct=1 / 128)
+    st = orc.Stencil(shape, seven(**w), CLAMP)
+    u = np.zeros(shape[::-1])
+    u[0, 0, 0] = 1.0
+    out = orc.sweep(st, np.zeros_like(u), u)
+    expect = np.zeros_like(u)
+    expect[0, 0, 0] = w["cc"] + w["cw"] + w["cn"] + w["cb"]
+    expect[0, 0, 1] = w["cw"]
+    expect[0, 1, 0] = w["cn"]
+    expect[1, 0, 0] = w["cb"]
+    np.testing.assert_array_equal(out, expect)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep_quadratic_field(orc, axis):
+    """u = s^2 along one axis, weights 1/4, 1/2, 1/4 along it: interior -> s^2 + 1/2,
+    clamped ends -> 1/4 (first) and (n-1)^2 - (n-1)/2 + 1/4 (last)."""
+    shape = (6, 7, 8)  # nx, ny, nz
+    nx, ny, nz = shape
+    n = (nx, ny, nz)[axis]
+    s = np.arange(n, dtype=np.float64) ** 2
+    pts = [(0, 0, 0, 0.5)]
+    d = [0, 0, 0]
+    d[axis] = 1
+    pts += [(-d[0], -d[1], -d[2], 0.25), (d[0], d[1], d[2], 0.25)]
+    # distractor weights on the other axes act on a constant field
+    st = orc.Stencil(shape, pts, CLAMP)
+    shp = [1, 1, 1]
+    shp[2 - axis] = n
+    u = np.broadcast_to(s.reshape(shp), (nz, ny, nx)).copy()
+    out = orc.sweep(st, np.zeros_like(u), u)
+    line = np.moveaxis(out, 2 - axis, 0)[:, 0, 0]
+    expect = s + 0.5
+    expect[0] = 0.5 * 0 + 0.25 * (0 + 1)
+    last = (n - 1) ** 2
+    expect[-1] = 0.5 * last + 0.25 * ((n - 2) ** 2 + last)
+    np.testing.assert_array_equal(line, expect)
+
+
+def test_sweep_conserves_total_when_clamped_symmetric(orc):
+    """Clamped boundary + symmetric pairs + weights summing to 1 + C = 0 conserve the sum."""
+    shape = (16, 12, 5)
+    st = orc.Stencil(shape, seven(1 / 2, 1 / 16, 1 / 16, 1 / 8, 1 / 8, 1 / 16, 1 / 16), CLAMP)
+    u = int_grid(shape, 2)
+    total = u.sum()
+    for _ in range(5):
+        u = orc.sweep(st, np.zeros_like(u), u)
+        assert u.sum() == total
+
+
+# ------------------------------------------------ Eq. (2), (3): checksums
+
+def test_checksums_match_numpy_sums(orc):
+    u = int_grid((13, 9, 4), 3)
+    a, b = orc.checksums(u)
+    np.testing.assert_array_equal(a, u.sum(axis=1))  # a[z][x] = sum over y
+    np.testing.assert_array_equal(b, u.sum(axis=2))  # b[z][y] = sum over x
+
+
+# ---------------------------------------------- Theorem 1 and Theorem 2
+
+ASYM = seven(3, 1, 2, 5, 1, 2, 4)  # integer, every opposite pair unequal
+
+
+@pytest.mark.parametrize("boundary", [CLAMP, PERIODIC, ZERO])
+@pytest.mark.parametrize("points", [ASYM, seven(2, 1, 1, 1, 1, 1, 1)], ids=["asym", "sym"])
+@pytest.mark.parametrize("shape", [(9, 7, 4), (5, 6, 1)], ids=["3d", "2d"])
+def test_theorem1_exact_on_integer_grids(orc, boundary, points, shape):
+    """Interpolated checksums equal the recomputed ones exactly (Theorem 1 / 2): integer
+    weights and values keep FP64 exact, so any dropped or misplaced boundary term shows."""
+    st = orc.Stencil(shape, points, boundary)
+    u = int_grid(shape, 4, hi=64)
+    C = int_grid(shape, 5, hi=16)
+    cx, cy = orc.checksums(C)
+    a, b = orc.checksums(u)
+    for _ in range(3):
+        un = orc.sweep(st, C, u)
+        an, bn = orc.checksums(un)
+        ap, bp = orc.interpolate(st, cx, cy, a, b, u)
+        np.testing.assert_array_equal(ap, an)
+        np.testing.assert_array_equal(bp, bn)
+        u, a, b = un, an, bn
+    assert np.abs(u).max() < 2 ** 52
+
+
+def test_theorem1_boundary_terms_nonzero_when_asymmetric(orc):
+    """With unequal opposite weights the simple form (Eq. 6/7) is wrong by exactly
+    (w_{y-1} - w_{y+1}) (u[y=0] - u[y=ny-1]) on a (clamped), and the x analogue on b."""
+    shape = (8, 6, 3)
+    st = orc.Stencil(shape, ASYM, CLAMP)
+    u = int_grid(shape, 6, hi=64)
+    C = int_grid(shape, 7, hi=16)
+    cx, cy = orc.checksums(C)
+    a, b = orc.checksums(u)
+    ap, bp = orc.interpolate(st, cx, cy, a, b, u)
+    sp_a, sp_b = orc.interpolate_simple(st, cx, cy, a, b)
+    cc, cw, ce, cn, cs, cb, ct = [w for *_, w in ASYM]
+    np.testing.assert_array_equal(ap - sp_a, (cn - cs) * (u[:, 0, :] - u[:, -1, :]))
+    np.testing.assert_array_equal(bp - sp_b, (cw - ce) * (u[:, :, 0] - u[:, :, -1]))
+
+
+@pytest.mark.parametrize("boundary", [CLAMP, PERIODIC])
+def test_simple_form_exact_when_boundary_terms_vanish(orc, boundary):
+    shape = (10, 9, 4)
+    st = orc.Stencil(shape, seven(2, 1, 1, 3, 3, 1, 1), boundary)
+    u = int_grid(shape, 8, hi=64)
+    C = int_grid(shape, 9, hi=16)
+    cx, cy = orc.checksums(C)
+    a, b = orc.checksums(u)
+    ap, bp = orc.interpolate_simple(st, cx, cy, a, b)
+    an, bn = orc.checksums(orc.sweep(st, C, u))
+    np.testing.assert_array_equal(ap, an)
+    np.testing.assert_array_equal(bp, bn)
+
+
+def test_paper_example_stencil_periodic(orc, golden):
+    """Sec. 3.1's 4-point average in 2D with periodic boundaries: applying it to the
+    checksum vectors gives a'_x = (a_{x-1} + a_{x+1})/4 + a_x/2 (two y-shifts keep a_x)."""
+    pts = [(i, j, 0, w) for i, j, w in golden["paper_claims"]["example_stencil_4pt_average"]["value"]]
+    # the printed set lists (i, j) = (0,-1), (-1,0), (1,0), (0,1)
+    shape = (12, 10, 1)
+    st = orc.Stencil(shape, pts, PERIODIC)
+    u = int_grid(shape, 10, hi=256)
+    a, b = orc.checksums(u)
+    zeros = np.zeros_like
+    ap, bp = orc.interpolate_simple(st, zeros(a), zeros(b), a, b)
+    np.testing.assert_array_equal(ap, (np.roll(a, 1, 1) + np.roll(a, -1, 1)) / 4 + a / 2)
+    np.testing.assert_array_equal(bp, (np.roll(b, 1, 1) + np.roll(b, -1, 1)) / 4 + b / 2)
+
+
+# ------------------------------------------------------- Sec. 3.4: detection
+
+def test_detect_threshold_semantics(orc):
+    comp = np.array([1.0, 1.0, 1.0, 1.0, 2.0, 1.0])
+    pred = np.array([1.0 + 2e-5, 1.0 + 0.5e-5, np.nan, np.inf, 2.0 - 3e-5, 1.0])
+    np.testing.assert_array_equal(orc.detect(pred, comp, 1e-5), [0, 2, 3, 4])
+
+
+# -------------------------------------------------- online method end to end
+
+def hotspot(orc, shape, seed):
+    co = inputs.hotspot_coeffs(*shape)
+    temp, power = inputs.grid_inputs(*shape, seed=seed)
+    st = orc.Stencil(shape, orc.hotspot_points(co))
+    return st, orc.source_term(power, co), temp
+
+
+@pytest.mark.parametrize("shape,steps", [((64, 64, 8), 128), ((512, 512, 8), 24)])
+def test_no_false_positives_at_paper_eps(orc, golden, shape, steps):
+    g = golden["paper_claims"]
+    assert list(shape) in g["false_positives_at_eps"]["tile_sizes"]
+    st, C, temp = hotspot(orc, shape, 0)
+    for mode in (orc.MODE_ONLINE, orc.MODE_OFFLINE):
+        r = orc.run(st, C, temp, steps, mode, eps=g["eps"]["value"])
+        assert r["n_events"] == g["false_positives_at_eps"]["value"]
+        assert r["max_resid"] < 1e-12
+
+
+def test_bit_detectability_matches_paper_64(orc, golden):
+    """Online at 64x64x8: flips in bits 0-12 pass unseen, bits 13-31 are located."""
+    g = golden["paper_claims"]
+    st, C, temp = hotspot(orc, (64, 64, 8), 1)
+    rng = np.random.default_rng(11)
+    for bit in range(32):
+        for trial in range(3):
+            z, y, x = int(rng.integers(8)), int(rng.integers(64)), int(rng.integers(64))
+            step = int(rng.integers(2, 30))
+            fl = inputs.flip_list([(step, 0, z, y, x, bit)])
+            r = orc.run(st, C, temp, 32, orc.MODE_ONLINE, fl)
+            assert not r["marginal"]
+            if bit in g["undetectable_bits_64x64x8"]["value"]:
+                assert r["n_events"] == 0, (bit, r["events"])
+            else:
+                assert bit in g["detectable_bits_64x64x8"]["value"]
+                ev = r["events"]
+                assert len(ev) == 1 and ev[0]["kind"] == orc.EV_CORRECTED
+                assert (ev[0]["step"], ev[0]["z"], ev[0]["y"], ev[0]["x"]) == (step, z, y, x)
+
+
+@pytest.mark.parametrize("bit", [13, 20, 27, 29, 30, 31])
+def test_online_correction_restores_fault_free_state(orc, bit):
+    st, C, temp = hotspot(orc, (48, 40, 6), 2)
+    ref = orc.run(st, C, temp, 20, orc.MODE_ONLINE)
+    fl = inputs.flip_list([(7, 0, 2, 17, 31, bit)])
+    r = orc.run(st, C, temp, 20, orc.MODE_ONLINE, fl)
+    assert r["n_events"] == 1
+    e = r["events"][0]
+    assert (e["z"], e["y"], e["x"]) == (2, 17, 31)
+    np.testing.assert_allclose(r["u"], ref["u"], rtol=1e-12, atol=0)
+
+
+def test_literal_eq8_loses_exponent_flips(orc):
+    """Evaluating Eq. (8) as a' - (a - u) cancels catastrophically after a high exponent
+    flip (the checksum 'overflow' of Sec. 5.3); the rearranged form does not."""
+    st, C, temp = hotspot(orc, (48, 40, 6), 2)
+    ref = orc.run(st, C, temp, 10, orc.MODE_ONLINE)
+    fl = inputs.flip_list([(3, 0, 1, 5, 6, 29)])
+    lit = orc.run(st, C, temp, 10, orc.MODE_ONLINE, fl, literal_eq8=True)
+    good = orc.run(st, C, temp, 10, orc.MODE_ONLINE, fl)
+    assert np.abs(lit["u"] - ref["u"]).max() > 1.0
+    assert np.abs(good["u"] - ref["u"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("target", [inputs.TARGET_A, inputs.TARGET_B])
+def test_checksum_corruption_leaves_grid_alone(orc, target):
+    """Fig. 4b: a corrupted checksum shows in one vector only; recomputing the flagged
+    line from u^t reproduces the same values and refreshes the checksum."""
+    st, C, temp = hotspot(orc, (32, 24, 4), 3)
+    ref = orc.run(st, C, temp, 8, orc.MODE_ONLINE)
+    fl = inputs.flip_list([(4, 0, 1, 9, 13, 27, target)])
+    r = orc.run(st, C, temp, 8, orc.MODE_ONLINE, fl)
+    np.testing.assert_array_equal(r["u"], ref["u"])
+    ev = r["events"]
+    assert len(ev) == 1 and ev[0]["kind"] == orc.EV_RECOMPUTED and ev[0]["step"] == 4
+    if target == inputs.TARGET_A:
+        assert (ev[0]["y"], ev[0]["x"]) == (-1, 13)
+    else:
+        assert (ev[0]["y"], ev[0]["x"]) == (9, -1)
+
+
+def test_two_by_two_pattern_is_recomputed_exactly(orc):
+    st, C, temp = hotspot(orc, (32, 24, 4), 4)
+    ref = orc.run(st, C, temp, 6, orc.MODE_ONLINE)
+    fl = inputs.flip_list([(2, 0, 1, 3, 4, 30), (2, 0, 1, 10, 20, 25)])
+    r = orc.run(st, C, temp, 6, orc.MODE_ONLINE, fl)
+    np.testing.assert_array_equal(r["u"], ref["u"])
+    lines = sorted((int(e["y"]), int(e["x"])) for e in r["events"])
+    assert lines == [(-1, 4), (-1, 20), (3, -1), (10, -1)]
+    assert all(e["kind"] == orc.EV_RECOMPUTED for e in r["events"])
+
+
+def test_same_row_pair_is_recomputed(orc):
+    st, C, temp = hotspot(orc, (32, 24, 4), 4)
+    ref = orc.run(st, C, temp, 6, orc.MODE_ONLINE)
+    fl = inputs.flip_list([(2, 0, 1, 3, 4, 30), (2, 0, 1, 3, 20, 25)])
+    r = orc.run(st, C, temp, 6, orc.MODE_ONLINE, fl)
+    np.testing.assert_array_equal(r["u"], ref["u"])
+
+
+# --------------------------------------------------------------- offline
+
+def test_offline_rollback_erases_detected_flip(orc, golden):
+    st, C, temp = hotspot(orc, (64, 64, 8), 5)
+    delta = golden["paper_claims"]["offline_period"]["value"]
+    ref = orc.run(st, C, temp, 40, orc.MODE_OFFLINE, delta=delta)
+    fl = inputs.flip_list([(20, 0, 3, 30, 40, 28)])
+    r = orc.run(st, C, temp, 40, orc.MODE_OFFLINE, fl, delta=delta)
+    assert r["n_rollbacks"] == 1
+    ev = r["events"]
+    assert len(ev) == 1 and ev[0]["kind"] == orc.EV_ROLLBACK and ev[0]["step"] == 16
+    np.testing.assert_array_equal(r["u"], ref["u"])
+
+
+def test_offline_matches_unprotected_when_fault_free(orc):
+    st, C, temp = hotspot(orc, (20, 18, 5), 6)
+    a = orc.run(st, C, temp, 37, orc.MODE_OFFLINE, delta=8)
+    b = orc.run(st, C, temp, 37, orc.MODE_NONE)
+    np.testing.assert_array_equal(a["u"], b["u"])
+    assert a["n_events"] == 0
+
+
+def test_offline_refuses_nonvanishing_boundary_terms(orc):
+    st = orc.Stencil((8, 8, 2), ASYM, CLAMP)
+    u = int_grid((8, 8, 2), 1)
+    with pytest.raises(RuntimeError):
+        orc.run(st, np.zeros_like(u), u, 4, orc.MODE_OFFLINE, delta=2)
+
+
+# ----------------------------------------------------------- flip schedule
+
+def test_splitmix64_published_first_output(orc, golden):
+    g = golden["splitmix64"]
+    assert orc.splitmix64(g["seed"], 0) == int(g["first_output"], 16)
+
+
+def test_schedule_statistics(orc):
+    shape = (64, 48, 8)
+    s = orc.schedule(7, 0.25, 0xFFFFFFFF, shape, 0, 20000)
+    assert abs(len(s) / 20000 - 0.25) < 0.02
+    assert s["x"].max() < 64 and s["y"].max() < 48 and s["z"].max() < 8
+    assert set(np.unique(s["bit"])) == set(range(32))
+    assert np.all(np.diff(s["step"]) >= 0)
+    many = orc.schedule(7, 3.5, 0x0000F000, shape, 0, 2000)
+    assert abs(len(many) / 2000 - 3.5) < 0.1
+    assert set(np.unique(many["bit"])) == {12, 13, 14, 15}
+    again = orc.schedule(7, 3.5, 0x0000F000, shape, 0, 2000)
+    np.testing.assert_array_equal(many, again)
+    assert len(orc.schedule(7, 0.0, 0xFFFFFFFF, shape, 0, 100)) == 0
+    assert len(orc.schedule(7, 1.0, 0, shape, 0, 100)) == 0
