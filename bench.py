@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the ABFT-protected HotSpot3D sweep on one GB300 (or N replicas).
+
+Workload (default): one 512x512x8 FP32 HotSpot3D grid with synthetic inputs
+(temperatures U[320,340] K, power U[0,1e-3]), 1000 online-protected sweeps per
+benchmark step with seeded bit flips at 1e-3 per sweep.  A benchmark step is one
+such 1000-sweep job (sweep, fused checksums, interpolation, detection, location,
+correction, injection).  Reported beside it: the unprotected sweep (overhead
+denominator) and the offline mode on the same grid, the dominant kernel's HBM
+roofline, the end-to-end job through the C ABI with host buffers, and the FP64
+CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it is launched by torch.distributed.run; each rank runs an independent
+replica (the grid does not shard across GPUs), value = all ranks' updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "protected GLUP/s, ABFT overhead % vs unprotected, HBM roofline fraction"
+WORKLOAD = "hotspot3d_512x512x8"
+SHAPE = (512, 512, 8)
+SWEEPS = 1000
+RATE = 1e-3
+BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="short run for profilers: warm-up jobs, then one protected and one plain job")
+    p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                   help="grid shape for --profile captures (default 512 512 8)")
+    p.add_argument("--sweeps", type=int, default=None, help="sweeps per job for --profile captures")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_sample(sweeps: int):
+    """The FP64 oracle on the same workload for `sweeps` online sweeps (single thread)."""
+    import oracle
+    from paper_1909_00709_gb300 import inputs
+    oracle.build()
+    co = inputs.hotspot_coeffs(*SHAPE)
+    temp, power = inputs.grid_inputs(*SHAPE, seed=1)
+    st = oracle.Stencil(SHAPE, oracle.hotspot_points(co))
+    C = oracle.source_term(power, co)
+    sched = oracle.schedule(1, RATE, 0xFFFFFFFF, SHAPE, 0, sweeps)
+    t0 = time.perf_counter()
+    oracle.run(st, C, temp, sweeps, oracle.MODE_ONLINE, sched)
+    return time.perf_counter() - t0
+
+
+def n_points():
+    return SHAPE[0] * SHAPE[1] * SHAPE[2]
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step a bounded 20-sweep sample of the workload."""
+    if rank != 0:
+        return
+    per = 20
+    for _ in range(args.warmup):
+        oracle_sample(per)
+    ts = [oracle_sample(per) for _ in range(args.steps)]
+    tot = sum(ts)
+    glups = n_points() * per * args.steps / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": per, "mode": "online",
+                       "flip_rate_per_sweep": RATE},
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} online sweeps of the {WORKLOAD} workload per step"},
+            "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_1909_00709_gb300 import abi, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    abi.lib(build_if_missing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    temp, power = inputs.grid_inputs(*SHAPE, seed=1)
+    co = inputs.hotspot_coeffs(*SHAPE)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed_jobs(ctx, mode, k):
+        """k jobs of SWEEPS sweeps; L2 flushed before each; device time of the jobs only."""
+        total = 0.0
+        for _ in range(k):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step(SWEEPS, mode)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            total += e0.elapsed_time(e1)
+        return total
+
+    prot = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
+    prot.inject(1, RATE, 0xFFFFFFFF)
+    plain = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
+    off = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
+    off.inject(1, RATE, 0xFFFFFFFF)
+
+    for _ in range(args.warmup):
+        prot.step(SWEEPS, abi.MODE_ONLINE)
+        plain.step(SWEEPS, abi.MODE_NONE)
+        off.step(SWEEPS, abi.MODE_OFFLINE)
+    torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    launches0 = prot.counters()["kernel_launches"]
+    barrier()
+    torch.cuda.synchronize(dev)
+    ms_prot = timed_jobs(prot, abi.MODE_ONLINE, args.steps)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = prot.counters()["kernel_launches"] - launches0
+    clk = clocks.stop()
+    ms_plain = timed_jobs(plain, abi.MODE_NONE, args.steps)
+    ms_off = timed_jobs(off, abi.MODE_OFFLINE, args.steps)
+    events = prot.events()
+    off_cnt = off.counters()
+
+    # dominant kernel: average launch duration from CUDA events on the launching stream
+    kt = prot.time_kernels(200, abi.MODE_ONLINE)
+    sweep_ms, sweep_n = kt["sweep_protected"]
+    sweep_avg_s = sweep_ms / sweep_n / 1e3
+    check_ms, check_n = kt["check_online"]
+    achieved = BYTES_PER_UPDATE * n_points() / sweep_avg_s / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # end to end through the public API with host buffers: upload, 1000 sweeps, read back
+    e2e = None
+    if not args.no_e2e:
+        host_t = torch.from_numpy(temp).pin_memory()
+        host_p = torch.from_numpy(power).pin_memory()
+        host_out = torch.empty(SHAPE[::-1], dtype=torch.float32).pin_memory()
+        walls = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            with abi.Context([SHAPE], [host_t], [host_p], [co], device=dev, stream=stream) as c:
+                c.inject(1, RATE, 0xFFFFFFFF)
+                c.step(SWEEPS, abi.MODE_ONLINE)
+                c.read(0, out=host_out)
+            walls.append(time.perf_counter() - t0)
+        wall = sum(walls[args.warmup:])
+        e2e = {"value": n_points() * SWEEPS * args.steps / wall / 1e9, "unit": "GLUP/s",
+               "h2d_bytes_per_step": 2 * n_points() * 4, "d2h_bytes_per_step": n_points() * 4,
+               "ms_per_step": wall / args.steps * 1e3}
+
+    # slowest rank decides
+    t_tot = torch.tensor([ms_prot], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
+    ms_max = float(t_tot.item())
+    value = world * n_points() * SWEEPS * args.steps / (ms_max / 1e3) / 1e9
+    if rank != 0:
+        return
+    plain_glups = n_points() * SWEEPS * args.steps / (ms_plain / 1e3) / 1e9
+    off_glups = n_points() * SWEEPS * args.steps / (ms_off / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu and world == 1:
+        sweeps = 200
+        t = oracle_sample(sweeps)
+        cpu = {"value": n_points() * sweeps / t / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sweeps} online sweeps of the {WORKLOAD} workload (seeded flips, 1e-3/sweep)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": SWEEPS, "mode": "online",
+                   "flip_rate_per_sweep": RATE, "eps": 1e-5, "checksum_acc": "fp32-tile/fp64",
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": "replicas"},
+        "overhead_pct": (ms_prot / ms_plain - 1.0) * 100.0,
+        "unprotected_glups": plain_glups,
+        "offline": {"glups": off_glups, "overhead_pct": (ms_off / ms_plain - 1.0) * 100.0, "delta": 16,
+                    "rollbacks": off_cnt["rollbacks"]},
+        "events": {"corrected": int((events["kind"] == 1).sum()), "recomputed": int((events["kind"] == 2).sum())},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_sweep<protected>",
+                     "avg_launch_us": sweep_avg_s * 1e6, "peak_source": peak_src,
+                     "check_kernel_avg_us": check_ms / max(check_n, 1) * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for c in (prot, plain, off):
+        c.close()
+
+
+def run_profile(args, local):
+    """Warm-up jobs, then one protected online job and one unprotected job; no output
+    beyond one summary line.  Used as the command under ncu."""
+    import torch
+    from paper_1909_00709_gb300 import abi, inputs
+    torch.cuda.set_device(local)
+    abi.lib(build_if_missing=True)
+    temp, power = inputs.grid_inputs(*SHAPE, seed=1)
+    co = inputs.hotspot_coeffs(*SHAPE)
+    prot = abi.Context([SHAPE], [temp], [power], [co])
+    prot.inject(1, RATE, 0xFFFFFFFF)
+    plain = abi.Context([SHAPE], [temp], [power], [co])
+    for _ in range(args.warmup):
+        prot.step(SWEEPS, abi.MODE_ONLINE)
+        plain.step(SWEEPS, abi.MODE_NONE)
+    prot.step(SWEEPS, abi.MODE_ONLINE)
+    plain.step(SWEEPS, abi.MODE_NONE)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": WORKLOAD, "shape": list(SHAPE), "sweeps": SWEEPS,
+                      "launches": prot.counters()["kernel_launches"] + plain.counters()["kernel_launches"]}))
+
+
+def main():
+    global SHAPE, SWEEPS, WORKLOAD
+    args = parse()
+    rank, world, local = dist_env()
+    if args.profile:
+        if args.shape:
+            SHAPE = tuple(args.shape)
+            WORKLOAD = "hotspot3d_%dx%dx%d" % SHAPE
+        if args.sweeps:
+            SWEEPS = args.sweeps
+        run_profile(args, local)
+        return
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * abft.h - C ABI of the GB300 (sm_103a) library for algorithm-based fault tolerance
+ * of 3D stencil sweeps, after Cavelan & Ciorba, "Algorithm-Based Fault Tolerance for
+ * Parallel Stencil Computations" (arXiv 1909.00709).
+ *
+ * What the library computes, per grid of nx*ny*nz FP32 points u[z][y][x]:
+ *   - the sweep of Eq. (1) with the 7-point HotSpot3D set S (centre, x-1, x+1, y-1,
+ *     y+1, z-1, z+1) and the constant term C = sdc*P + c_amb*t_amb, with clamped
+ *     boundaries (an out-of-range neighbour is the centre, Fig. 2);
+ *   - per-plane row and column checksums a[z][x] = sum_y u, b[z][y] = sum_x u
+ *     (Eq. 2, 3), fused into the sweep;
+ *   - the interpolated checksums of Theorem 1 (Eq. 4, 5; boundary terms alpha, beta
+ *     in closed form for the clamped rule), the relative test of Sec. 3.4, location
+ *     at the intersection of the failing row and column, and the correction of
+ *     Eq. (8) / Fig. 9, every sweep (online mode, Sec. 3);
+ *   - the offline mode of Sec. 4: a checkpoint every Delta sweeps, Theorem 1 chained
+ *     Delta times (Fig. 10), one comparison per window and rollback on a mismatch.
+ *
+ * Conventions for every call:
+ *   - Every function returns an abft_status and never throws or aborts.  On failure
+ *     abft_last_error(ctx) holds a one-line message.
+ *   - Device memory is owned by the caller.  abft_init borrows one device workspace
+ *     of at least abft_workspace_bytes() bytes for the lifetime of the context; the
+ *     library itself never calls cudaMalloc.  Host-side state (schedules, graphs,
+ *     the context) is owned by the library and freed by abft_destroy.
+ *   - All device work is enqueued on opt->stream (a cudaStream_t; NULL = the
+ *     legacy default stream).  Calls that return device results to the host
+ *     (abft_step, abft_verify, abft_correct, abft_events, abft_read) synchronise that
+ *     stream before returning.
+ *   - Arrays are row-major with x fastest: index (z*ny + y)*nx + x.
+ *   - Not thread-safe: one host thread per context at a time.
+ */
+#ifndef ABFT_H
+#define ABFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ABFT_API __attribute__((visibility("default")))
+#else
+#define ABFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct abft_ctx abft_ctx; /* opaque, library-owned */
+
+typedef enum {
+  ABFT_OK = 0,
+  ABFT_E_INVAL = 1,         /* an argument is out of range or inconsistent */
+  ABFT_E_CUDA = 2,          /* a CUDA runtime call failed */
+  ABFT_E_NOMEM = 3,         /* workspace smaller than abft_workspace_bytes(), or host allocation failed */
+  ABFT_E_STATE = 4,         /* the call is not valid in the context's current state */
+  ABFT_E_TIMEOUT = 5,       /* a bounded device-side wait gave up; the context is poisoned */
+  ABFT_E_UNCORRECTABLE = 6, /* a mismatch survived correction (offline: the recomputed window failed too) */
+  ABFT_E_TRUNCATED = 7      /* more events than event_capacity; the first ones were kept */
+} abft_status;
+
+typedef enum {
+  ABFT_MODE_NONE = 0,    /* unprotected sweeps (the paper's No-ABFT baseline) */
+  ABFT_MODE_ONLINE = 1,  /* detect and correct after every sweep (Sec. 3) */
+  ABFT_MODE_OFFLINE = 2  /* detect every Delta sweeps, roll back on a mismatch (Sec. 4) */
+} abft_mode;
+
+typedef enum {
+  ABFT_ACC_FP32 = 0,     /* FP32 tile sums, FP64 across tiles */
+  ABFT_ACC_TWOSUM = 1,   /* compensated (TwoSum) FP32 tile sums, FP64 across tiles */
+  ABFT_ACC_FP64 = 2      /* FP64 accumulation from the first add */
+} abft_acc;
+
+typedef enum {
+  ABFT_EV_CORRECTED = 1,  /* Eq. (8) applied at (z, y, x); before/after hold the values */
+  ABFT_EV_RECOMPUTED = 2, /* a flagged line recomputed from u^t: row y (x = -1) or column x (y = -1) */
+  ABFT_EV_ROLLBACK = 3    /* offline window starting at `step` restored and recomputed */
+} abft_event_kind;
+
+/* one grid; the library pads rows to a pitch that is a multiple of 32 elements */
+typedef struct { int32_t nx, ny, nz; } abft_grid;
+
+/* Stencil weights of Eq. (1) (cw/ce: x-1/x+1, cn/cs: y-1/y+1, cb/ct: z-1/z+1) and
+   the source-term constants C = sdc*P + c_amb*t_amb. */
+typedef struct { float cc, cw, ce, cn, cs, cb, ct, sdc, c_amb, t_amb; } abft_coeffs;
+
+typedef struct {
+  double eps;               /* detection threshold of Sec. 3.4 (paper: 1e-5) */
+  int32_t delta;            /* offline detection period (paper: 16) */
+  int32_t acc;              /* abft_acc */
+  int32_t event_capacity;   /* events kept on the device (>= 1) */
+  int32_t graph_steps;      /* sweeps per captured CUDA graph; 0 disables graphs */
+  int32_t tile_y;           /* rows per sweep tile (8, 16 or 32); 0 = library default */
+  int32_t max_flips_per_step; /* schedule capacity per step and grid (<= 511) */
+  void* stream;             /* cudaStream_t used for all device work */
+} abft_options;
+
+/* an event recorded on the device */
+typedef struct {
+  int64_t step;                 /* sweep index whose output was checked (window start for rollbacks) */
+  int32_t grid, z, y, x, kind;  /* abft_event_kind; -1 marks "whole line/window" */
+  float before, after;          /* Eq. (8) values; rollback: flagged entries / window length */
+} abft_event;
+
+/* a scheduled bit flip: XOR bit `bit` (0..31) of the FP32 result of point (z, y, x)
+   of grid `grid` at sweep `step`, after the update and before it is stored (Sec. 5.1);
+   target 0 = grid point (others reserved) */
+typedef struct { int64_t step; int32_t grid, z, y, x, bit, target; } abft_flip;
+
+typedef struct {
+  int64_t steps_done;       /* sweeps committed so far */
+  int64_t kernel_launches;  /* kernels this context launched (graph nodes counted) */
+  int64_t events;           /* events recorded (may exceed event_capacity) */
+  int64_t rollbacks;        /* offline windows recomputed */
+  int64_t flips_scheduled;  /* flips handed to the device */
+} abft_counters;
+
+/* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
+   sweeps, default tile, 64 flips per step, NULL stream. */
+ABFT_API void abft_default_options(abft_options* opt);
+
+/* Bytes of device workspace abft_init needs for these grids and options
+   (0 if the arguments are invalid). */
+ABFT_API size_t abft_workspace_bytes(const abft_grid* grids, int32_t n_grids, const abft_options* opt);
+
+/* Create a context for n_grids independent grids (Sec. 3.1's state u and constant
+   term C, Table 1's eps and Delta).  temp[g] and power[g] point to nx*ny*nz FP32
+   values each, in host or device memory (copied, not kept).  coeffs[g] holds grid
+   g's weights and source constants.  The initial checksums a^0, b^0 and the
+   constant-term checksums c_x, c_y of Theorem 1 are computed here.  workspace is
+   device memory, 256-byte aligned, borrowed until abft_destroy.
+   Errors: ABFT_E_INVAL (bad sizes, NULL pointers, misaligned workspace, offline-
+   incapable weights are allowed but later OFFLINE steps fail), ABFT_E_NOMEM,
+   ABFT_E_CUDA. */
+ABFT_API abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids,
+                      const float* const* temp, const float* const* power,
+                      const abft_coeffs* coeffs, const abft_options* opt,
+                      void* workspace, size_t workspace_bytes);
+
+/* Advance every grid by n sweeps in the given mode (abft_mode).  ONLINE checks and
+   corrects after each sweep (Sec. 3.2-3.5).  OFFLINE runs windows of Delta sweeps
+   (the last one may be shorter), compares once per window and recomputes a
+   window from its checkpoint on a mismatch (Sec. 4); it needs cn == cs and
+   cw == ce (the boundary terms vanish) and returns ABFT_E_INVAL otherwise.
+   Synchronises the stream at the end.  Errors: ABFT_E_INVAL, ABFT_E_CUDA,
+   ABFT_E_TIMEOUT, ABFT_E_UNCORRECTABLE, ABFT_E_TRUNCATED (events dropped; the
+   sweeps still completed). */
+ABFT_API abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode);
+
+/* Theorem 2 on demand: recompute the checksums of the current state and compare
+   them with the interpolated ones (chained over the sweeps made since the last
+   verified state, Sec. 4.1).  *n_mismatch receives the number of failing entries. */
+ABFT_API abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch);
+
+/* Correct what the last abft_verify found: Eq. (8) at single row/column
+   intersections when the state is one sweep or less past the verified one,
+   otherwise roll back to the verified state and recompute (Sec. 4.2).
+   *n_fixed receives the number of corrected points or recomputed sweeps. */
+ABFT_API abft_status abft_correct(abft_ctx* ctx, int64_t* n_fixed);
+
+/* Seeded random bit flips from the next sweep on (Sec. 5.1's injection): `rate` is the
+   expected number of flips per sweep and grid (floor(rate) plus one with
+   probability frac(rate)), points uniform over the grid, bits uniform over the set
+   bits of `bitmask`, drawn by SplitMix64 (see abft_schedule).  rate 0 disables. */
+ABFT_API abft_status abft_inject(abft_ctx* ctx, uint64_t seed, double rate, uint32_t bitmask);
+
+/* An explicit flip list (replaces any seeded schedule); entries are copied. */
+ABFT_API abft_status abft_inject_list(abft_ctx* ctx, const abft_flip* flips, int64_t n);
+
+/* The seeded schedule of one grid for sweeps [t_begin, t_end): the flips abft_inject
+   would apply.  Pure host function, no context needed.  Returns the number of
+   flips (entries beyond cap are not written), or -1 on invalid arguments. */
+ABFT_API int64_t abft_schedule(uint64_t seed, double rate, uint32_t bitmask, int32_t grid,
+                      int32_t n_grids, int32_t nx, int32_t ny, int32_t nz,
+                      int64_t t_begin, int64_t t_end, abft_flip* out, int64_t cap);
+
+/* Copy up to cap recorded events to host memory; *n_out = number recorded (may
+   exceed cap).  Returns ABFT_E_TRUNCATED when the device log overflowed. */
+ABFT_API abft_status abft_events(abft_ctx* ctx, abft_event* buf, int64_t cap, int64_t* n_out);
+
+/* Copy grid g's current state (nx*ny*nz FP32, unpadded) to dst (host or device). */
+ABFT_API abft_status abft_read(abft_ctx* ctx, int32_t grid, float* dst);
+
+/* Device pointer and row pitch (elements) of grid g's current state, valid until
+   the next abft_step/abft_correct. */
+ABFT_API abft_status abft_current(abft_ctx* ctx, int32_t grid, float** dev_ptr, int64_t* pitch);
+
+ABFT_API abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out);
+
+/* Measurement hook: run n sweeps of `mode` without graphs, bracketing every kernel
+   launch with CUDA events on the context stream, and report per kernel kind the
+   summed milliseconds and launch counts (arrays of length ABFT_KERNEL_KINDS, in the
+   order sweep-plain, sweep-protected, check-online, check-offline, chain, other). */
+#define ABFT_KERNEL_KINDS 6
+ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, double* ms, int64_t* launches);
+
+ABFT_API const char* abft_last_error(const abft_ctx* ctx);
+ABFT_API const char* abft_status_string(abft_status s);
+
+/* Release host state and graphs; the workspace is the caller's to free. */
+ABFT_API void abft_destroy(abft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABFT_H */

@@ -1,0 +1,280 @@
+"""ctypes binding of the C ABI in include/abft.h (argument marshalling only).
+
+Every compute step runs inside libabft.so on the GPU.  PyTorch is used for the
+device workspace and the CUDA stream; nothing here computes any part of the
+method.  If the library has not been built, ``lib()`` raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MODE_NONE, MODE_ONLINE, MODE_OFFLINE = 0, 1, 2
+ACC_FP32, ACC_TWOSUM, ACC_FP64 = 0, 1, 2
+EV_CORRECTED, EV_RECOMPUTED, EV_ROLLBACK = 1, 2, 3
+KERNEL_KINDS = ("sweep_plain", "sweep_protected", "check_online", "check_offline", "chain", "other")
+
+STATUS = {0: "ABFT_OK", 1: "ABFT_E_INVAL", 2: "ABFT_E_CUDA", 3: "ABFT_E_NOMEM", 4: "ABFT_E_STATE",
+          5: "ABFT_E_TIMEOUT", 6: "ABFT_E_UNCORRECTABLE", 7: "ABFT_E_TRUNCATED"}
+
+EXPORTS = ("abft_default_options", "abft_workspace_bytes", "abft_init", "abft_step", "abft_verify",
+           "abft_correct", "abft_inject", "abft_inject_list", "abft_schedule", "abft_events",
+           "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
+           "abft_last_error", "abft_status_string", "abft_destroy")
+
+
+class abft_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32)]
+
+
+class abft_coeffs(ct.Structure):
+    _fields_ = [(n, ct.c_float) for n in ("cc", "cw", "ce", "cn", "cs", "cb", "ct", "sdc", "c_amb", "t_amb")]
+
+
+class abft_options(ct.Structure):
+    _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
+                ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
+                ("max_flips_per_step", ct.c_int32), ("stream", ct.c_void_p)]
+
+
+class abft_counters(ct.Structure):
+    _fields_ = [("steps_done", ct.c_int64), ("kernel_launches", ct.c_int64), ("events", ct.c_int64),
+                ("rollbacks", ct.c_int64), ("flips_scheduled", ct.c_int64)]
+
+
+class abft_event(ct.Structure):
+    _fields_ = [("step", ct.c_int64), ("grid", ct.c_int32), ("z", ct.c_int32), ("y", ct.c_int32),
+                ("x", ct.c_int32), ("kind", ct.c_int32), ("before", ct.c_float), ("after", ct.c_float)]
+
+
+class abft_flip(ct.Structure):
+    _fields_ = [("step", ct.c_int64), ("grid", ct.c_int32), ("z", ct.c_int32), ("y", ct.c_int32),
+                ("x", ct.c_int32), ("bit", ct.c_int32), ("target", ct.c_int32)]
+
+
+# numpy views of the C structs (the C compiler pads abft_event to 40 bytes)
+EVENT = np.dtype([("step", "<i8"), ("grid", "<i4"), ("z", "<i4"), ("y", "<i4"), ("x", "<i4"),
+                  ("kind", "<i4"), ("before", "<f4"), ("after", "<f4")], align=True)
+FLIP = np.dtype([("step", "<i8"), ("grid", "<i4"), ("z", "<i4"), ("y", "<i4"), ("x", "<i4"),
+                 ("bit", "<i4"), ("target", "<i4")])
+
+_lib = None
+
+
+class AbftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib(build_if_missing: bool = False):
+    """Load libabft.so (in-tree build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {path} is not built; call __graft_entry__.build() "
+                               "or paper_1909_00709_gb300.build.build()")
+        _build.build()
+    L = ct.CDLL(path)
+    P, I32, I64, U64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_uint64
+    L.abft_default_options.argtypes = [ct.POINTER(abft_options)]
+    L.abft_default_options.restype = None
+    L.abft_workspace_bytes.argtypes = [ct.POINTER(abft_grid), I32, ct.POINTER(abft_options)]
+    L.abft_workspace_bytes.restype = ct.c_size_t
+    L.abft_init.argtypes = [ct.POINTER(P), ct.POINTER(abft_grid), I32, ct.POINTER(P), ct.POINTER(P),
+                            ct.POINTER(abft_coeffs), ct.POINTER(abft_options), P, ct.c_size_t]
+    L.abft_step.argtypes = [P, I64, I32]
+    L.abft_verify.argtypes = [P, ct.POINTER(I64)]
+    L.abft_correct.argtypes = [P, ct.POINTER(I64)]
+    L.abft_inject.argtypes = [P, U64, ct.c_double, ct.c_uint32]
+    L.abft_inject_list.argtypes = [P, P, I64]
+    L.abft_schedule.argtypes = [U64, ct.c_double, ct.c_uint32, I32, I32, I32, I32, I32, I64, I64, P, I64]
+    L.abft_schedule.restype = I64
+    L.abft_events.argtypes = [P, P, I64, ct.POINTER(I64)]
+    L.abft_read.argtypes = [P, I32, P]
+    L.abft_current.argtypes = [P, I32, ct.POINTER(P), ct.POINTER(I64)]
+    L.abft_get_counters.argtypes = [P, ct.POINTER(abft_counters)]
+    L.abft_time_kernels.argtypes = [P, I64, I32, P, P]
+    L.abft_last_error.argtypes = [P]
+    L.abft_last_error.restype = ct.c_char_p
+    L.abft_status_string.argtypes = [ct.c_int]
+    L.abft_status_string.restype = ct.c_char_p
+    L.abft_destroy.argtypes = [P]
+    L.abft_destroy.restype = None
+    for name in ("abft_init", "abft_step", "abft_verify", "abft_correct", "abft_inject", "abft_inject_list",
+                 "abft_events", "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels"):
+        getattr(L, name).restype = ct.c_int
+    _lib = L
+    return L
+
+
+# ------------------------------------------------------------ plain wrappers
+
+def abft_default_options(**kw) -> abft_options:
+    o = abft_options()
+    lib().abft_default_options(ct.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _grids(shapes):
+    arr = (abft_grid * len(shapes))()
+    for i, (nx, ny, nz) in enumerate(shapes):
+        arr[i] = abft_grid(nx, ny, nz)
+    return arr
+
+
+def abft_workspace_bytes(shapes, opt: abft_options) -> int:
+    return int(lib().abft_workspace_bytes(_grids(shapes), len(shapes), ct.byref(opt)))
+
+
+def abft_schedule(seed: int, rate: float, bitmask: int, shape, t_begin: int, t_end: int,
+                  grid: int = 0, n_grids: int = 1, cap: int = 1 << 20) -> np.ndarray:
+    nx, ny, nz = shape
+    out = np.zeros(cap, dtype=FLIP)
+    n = lib().abft_schedule(seed & (2**64 - 1), rate, bitmask, grid, n_grids, nx, ny, nz, t_begin, t_end,
+                            out.ctypes.data, cap)
+    if n < 0:
+        raise AbftError(1, "abft_schedule: invalid arguments")
+    return out[:min(n, cap)].copy()
+
+
+def abft_status_string(s: int) -> str:
+    return lib().abft_status_string(s).decode()
+
+
+def _coeffs(co: dict) -> abft_coeffs:
+    return abft_coeffs(*[co[n] for n in ("cc", "cw", "ce", "cn", "cs", "cb", "ct", "sdc", "c_amb", "t_amb")])
+
+
+class Context:
+    """One abft_ctx plus the torch-allocated device workspace it borrows.
+
+    Methods are named after the C calls they wrap (abft_step -> step, ...)."""
+
+    def __init__(self, shapes, temps, powers, coeffs, *, device=None, stream=None, **opt_kw):
+        import torch
+        self._torch = torch
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        n = len(self.shapes)
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opt = abft_default_options(**opt_kw)
+        opt.stream = self.stream.cuda_stream
+        self.opt = opt
+        nbytes = abft_workspace_bytes(self.shapes, opt)
+        if nbytes == 0:
+            raise AbftError(1, "invalid grid shapes or options")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._keep = []
+        tp = (ct.c_void_p * n)()
+        pp = (ct.c_void_p * n)()
+        for i in range(n):
+            tp[i] = self._ptr(temps[i])
+            pp[i] = self._ptr(powers[i])
+        cos = (abft_coeffs * n)(*[_coeffs(c) for c in coeffs])
+        h = ct.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib().abft_init(ct.byref(h), _grids(self.shapes), n, tp, pp, cos, ct.byref(opt),
+                                 ct.c_void_p(self.workspace.data_ptr()), nbytes)
+        if st != 0:
+            raise AbftError(st, "abft_init failed")
+        self._keep.clear()
+        self.h = h
+
+    def _ptr(self, a):
+        torch = self._torch
+        if isinstance(a, torch.Tensor):
+            assert a.dtype == torch.float32 and a.is_contiguous()
+            self._keep.append(a)
+            return a.data_ptr()
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        self._keep.append(a)
+        return a.ctypes.data
+
+    def _check(self, st: int, what: str, ok=(0,)):
+        if st not in ok:
+            raise AbftError(st, f"{what}: {lib().abft_last_error(self.h).decode()}")
+        return st
+
+    def step(self, n: int, mode: int) -> int:
+        return self._check(lib().abft_step(self.h, n, mode), "abft_step", ok=(0, 7))
+
+    def verify(self) -> int:
+        v = ct.c_int64()
+        self._check(lib().abft_verify(self.h, ct.byref(v)), "abft_verify")
+        return v.value
+
+    def correct(self) -> int:
+        v = ct.c_int64()
+        self._check(lib().abft_correct(self.h, ct.byref(v)), "abft_correct")
+        return v.value
+
+    def inject(self, seed: int, rate: float, bitmask: int = 0xFFFFFFFF):
+        self._check(lib().abft_inject(self.h, seed & (2**64 - 1), rate, bitmask), "abft_inject")
+
+    def inject_list(self, flips: np.ndarray):
+        fl = np.zeros(len(flips), dtype=FLIP)
+        for name in FLIP.names:
+            fl[name] = flips[name] if name in flips.dtype.names else 0
+        self._check(lib().abft_inject_list(self.h, fl.ctypes.data if len(fl) else None, len(fl)),
+                    "abft_inject_list")
+
+    def events(self, cap: int = 1 << 16) -> np.ndarray:
+        buf = np.zeros(cap, dtype=EVENT)
+        n = ct.c_int64()
+        self._check(lib().abft_events(self.h, buf.ctypes.data, cap, ct.byref(n)), "abft_events", ok=(0, 7))
+        return buf[:min(n.value, cap)].copy()
+
+    def read(self, grid: int = 0, out=None) -> np.ndarray:
+        nx, ny, nz = self.shapes[grid]
+        if out is None:
+            out = np.empty((nz, ny, nx), dtype=np.float32)
+        ptr = out.data_ptr() if isinstance(out, self._torch.Tensor) else out.ctypes.data
+        self._check(lib().abft_read(self.h, grid, ct.c_void_p(ptr)), "abft_read")
+        return out
+
+    def current(self, grid: int = 0):
+        p = ct.c_void_p()
+        pitch = ct.c_int64()
+        self._check(lib().abft_current(self.h, grid, ct.byref(p), ct.byref(pitch)), "abft_current")
+        return p.value, pitch.value
+
+    def counters(self) -> dict:
+        c = abft_counters()
+        self._check(lib().abft_get_counters(self.h, ct.byref(c)), "abft_get_counters")
+        return {k: getattr(c, k) for k, _ in abft_counters._fields_}
+
+    def time_kernels(self, n: int, mode: int) -> dict:
+        ms = (ct.c_double * 6)()
+        la = (ct.c_int64 * 6)()
+        self._check(lib().abft_time_kernels(self.h, n, mode, ms, la), "abft_time_kernels", ok=(0, 7))
+        return {k: (ms[i], la[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().abft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,928 @@
+// Host side of the C ABI declared in include/abft.h: context and workspace layout,
+// seeded flip schedules, and the drivers of the online (Sec. 3) and offline
+// (Sec. 4) modes.  No device memory is allocated here: everything lives in the
+// caller's workspace.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "abft_internal.h"
+
+using namespace abft;
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// bump allocator over the caller's workspace
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = align_up(off, 256);
+    const size_t at = off;
+    off += align_up(bytes ? bytes : 1, 256);
+    return at;
+  }
+};
+
+struct GridPlan {
+  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, fcnt, fidx;
+};
+
+struct Plan {
+  std::vector<GridPlan> g;
+  size_t ctrl, gctrl, events, flips, off, total;
+  int64_t sched_cap;
+};
+
+int pick_ty(const abft_options& o) { return o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32 ? o.tile_y : 16; }
+
+size_t partial_elem(int acc) { return acc == ABFT_ACC_FP32 ? 4 : 8; }
+
+bool valid_grid(const abft_grid& g) {
+  return g.nx >= 1 && g.ny >= 1 && g.nz >= 1 && g.nx <= (1 << 20) && g.ny <= (1 << 20) && g.nz <= 65535 &&
+         (int64_t)g.nx * g.ny * g.nz <= (int64_t)1 << 34;
+}
+
+bool valid_options(const abft_options& o) {
+  return o.eps > 0 && std::isfinite(o.eps) && o.delta >= 1 && o.acc >= 0 && o.acc <= 2 &&
+         o.event_capacity >= 1 && o.graph_steps >= 0 && o.max_flips_per_step >= 0 &&
+         o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32);
+}
+
+bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
+  if (!grids || n < 1 || !valid_options(o)) return false;
+  Bump b;
+  const int ty = pick_ty(o);
+  P->g.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const abft_grid& G = grids[i];
+    if (!valid_grid(G)) return false;
+    const size_t px = align_up(G.nx, 32);
+    const size_t vol = px * G.ny * G.nz * sizeof(float);
+    const size_t na = (size_t)G.nz * G.nx * 8, nb = (size_t)G.nz * G.ny * 8;
+    const size_t ntx = (G.nx + kTX - 1) / kTX, nty = (G.ny + ty - 1) / ty;
+    GridPlan& p = P->g[i];
+    for (int k = 0; k < 3; ++k) p.u[k] = b.take(vol);
+    p.C = b.take(vol);
+    p.cx = b.take(na);
+    p.cy = b.take(nb);
+    for (int k = 0; k < 3; ++k) { p.A[k] = b.take(na); p.B[k] = b.take(nb); }
+    for (int k = 0; k < 3; ++k) { p.AP[k] = b.take(na); p.BP[k] = b.take(nb); }
+    p.PA = b.take(nty * G.nz * ntx * kTX * partial_elem(o.acc));
+    p.PB = b.take(ntx * G.nz * (size_t)G.ny * partial_elem(o.acc));
+    p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
+    p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
+  }
+  P->ctrl = b.take(sizeof(DevCtrl));
+  P->gctrl = b.take(sizeof(DevGridCtrl) * n);
+  P->events = b.take(sizeof(abft_event) * (size_t)o.event_capacity);
+  P->sched_cap = std::max<int64_t>(1 << 16, (int64_t)o.max_flips_per_step * n * 64);
+  P->flips = b.take(sizeof(DevFlip) * P->sched_cap);
+  P->off = b.take(sizeof(int) * (kSchedSteps + 1));
+  P->total = align_up(b.off, 256);
+  return true;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output k of the stream seeded with `seed`
+struct SplitMix64 {
+  uint64_t seed;
+  uint64_t at(uint64_t k) const {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (k + 1);
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+};
+
+// Seeded flips of one (grid, sweep): counter block (t*n_grids + grid)*1024; draw 0 sets
+// the count floor(rate) + Bernoulli(frac(rate)), draws 1+2i / 2+2i the point and the bit.
+void seeded_flips(uint64_t seed, double rate, uint32_t mask, int grid, int n_grids, const abft_grid& G,
+                  int64_t t, std::vector<abft_flip>* out) {
+  if (rate <= 0.0 || mask == 0) return;
+  const SplitMix64 r{seed};
+  const uint64_t base = ((uint64_t)t * (uint64_t)n_grids + (uint64_t)grid) << 10;
+  const double whole = std::floor(rate);
+  const uint64_t threshold = (uint64_t)((rate - whole) * 9007199254740992.0);
+  int64_t count = (int64_t)whole + ((r.at(base) >> 11) < threshold ? 1 : 0);
+  count = std::min<int64_t>(count, 511);
+  int bits[32], nbits = 0;
+  for (int b = 0; b < 32; ++b)
+    if (mask & (1u << b)) bits[nbits++] = b;
+  const uint64_t npts = (uint64_t)G.nx * G.ny * G.nz;
+  for (int64_t i = 0; i < count; ++i) {
+    const uint64_t p = (uint64_t)(((unsigned __int128)r.at(base + 1 + 2 * i) * npts) >> 64);
+    const uint64_t j = ((r.at(base + 2 + 2 * i) >> 32) * (uint64_t)nbits) >> 32;
+    abft_flip f;
+    f.step = t;
+    f.grid = grid;
+    f.x = (int32_t)(p % (uint64_t)G.nx);
+    f.y = (int32_t)((p / (uint64_t)G.nx) % (uint64_t)G.ny);
+    f.z = (int32_t)(p / ((uint64_t)G.nx * G.ny));
+    f.bit = bits[j];
+    f.target = 0;
+    out->push_back(f);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+namespace abft {
+
+cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUtensorMap* tm_c, char* err,
+                             size_t errlen) {
+  auto enc = encode_fn();
+  if (!enc) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
+    return cudaErrorNotSupported;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.ny * 4};
+  cuuint32_t ebox[3] = {1, 1, 1};
+  cuuint32_t ubox[3] = {(cuuint32_t)kUW, (cuuint32_t)(ty + 2), 1};
+  cuuint32_t cbox[3] = {(cuuint32_t)kTX, (cuuint32_t)ty, 1};
+  for (int k = 0; k < 4; ++k) {
+    CUtensorMap* m = k < 3 ? &tm_u[k] : tm_c;
+    void* base = k < 3 ? (void*)g.u[k] : (void*)g.C;
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, k < 3 ? ubox : cbox, ebox,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+      return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace abft
+
+struct abft_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  abft_options opt{};
+  int n = 0;
+  std::vector<abft_grid> grids;
+  std::vector<abft_coeffs> co;
+  std::vector<GridDev> g;
+  std::vector<CUtensorMap> tm_u, tm_c;
+  std::vector<int> cur, ref;
+  std::vector<int64_t> ref_step;
+  std::vector<char> ck_valid;
+  int64_t step = 0;
+  DevCtrl* ctrl = nullptr;
+  DevGridCtrl* gctrl = nullptr;
+  abft_event* events = nullptr;
+  DevFlip* d_flips = nullptr;
+  int* d_off = nullptr;
+  int64_t sched_cap = 0;
+  // injection
+  int inj_kind = 0;  // 0 none, 1 seeded, 2 list
+  uint64_t seed = 0;
+  double rate = 0;
+  uint32_t mask = 0;
+  std::vector<abft_flip> list;
+  int64_t sched_t0 = 0, sched_n = 0;  // what the device currently holds
+  bool sched_live = false;
+  // pinned host staging
+  DevFlip* h_flips = nullptr;
+  int* h_off = nullptr;
+  DevCtrl* h_ctrl = nullptr;
+  DevGridCtrl* h_gctrl = nullptr;
+  abft_event* h_ev = nullptr;
+  // verify state
+  bool verified = false;
+  std::vector<int64_t> v_dist;
+  std::vector<unsigned long long> v_fail;
+  // timing hook
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  // counters
+  int64_t launches = 0, rollbacks = 0, flips_scheduled = 0;
+  unsigned status_seen = 0;
+  std::string err;
+};
+
+namespace {
+
+abft_status fail(abft_ctx* c, abft_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, ABFT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+Launch launcher(abft_ctx* ctx) {
+  Launch L;
+  L.s = ctx->stream;
+  L.ctrl = ctx->ctrl;
+  L.events = ctx->events;
+  L.sched.flips = ctx->d_flips;
+  L.sched.off = ctx->d_off;
+  return L;
+}
+
+// every kernel launch goes through here: counted, and bracketed by events when timing
+template <class F>
+cudaError_t run(abft_ctx* ctx, int kind, F&& f) {
+  if (ctx->timing) {
+    if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ctx->ev_pool.push_back(e);
+      }
+    }
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream);
+    const cudaError_t r = f();
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used + 1], ctx->stream);
+    ctx->ev_kind.push_back(kind);
+    ctx->ev_used += 2;
+    ++ctx->launches;
+    return r;
+  }
+  ++ctx->launches;
+  return f();
+}
+
+int other_than(int a, int b) {
+  for (int k = 0; k < 3; ++k)
+    if (k != a && k != b) return k;
+  return -1;
+}
+
+bool offline_capable(const abft_coeffs& c) { return c.cn == c.cs && c.cw == c.ce; }
+
+// upload the flips of sweeps [t0, t0 + n) (n <= kSchedSteps); returns the number of
+// sweeps actually covered (less than n when the capacity runs out)
+abft_status upload_schedule(abft_ctx* ctx, int64_t t0, int64_t n, int64_t* covered) {
+  *covered = n;
+  if (ctx->inj_kind == 0) {
+    if (ctx->sched_live) {
+      ctx->h_ctrl->sched_n = 0;
+      CK(cudaMemcpyAsync(&ctx->ctrl->sched_n, &ctx->h_ctrl->sched_n, sizeof(int), cudaMemcpyHostToDevice,
+                         ctx->stream));
+      ctx->sched_live = false;
+    }
+    return ABFT_OK;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));  // staging buffers are about to be rewritten
+  std::vector<abft_flip> fl;
+  int64_t total = 0;
+  int64_t t = t0;
+  ctx->h_off[0] = 0;
+  for (; t < t0 + n; ++t) {
+    fl.clear();
+    if (ctx->inj_kind == 1) {
+      for (int gi = 0; gi < ctx->n; ++gi)
+        seeded_flips(ctx->seed, ctx->rate, ctx->mask, gi, ctx->n, ctx->grids[gi], t, &fl);
+    } else {
+      auto lo = std::lower_bound(ctx->list.begin(), ctx->list.end(), t,
+                                 [](const abft_flip& f, int64_t s) { return f.step < s; });
+      for (auto it = lo; it != ctx->list.end() && it->step == t; ++it) fl.push_back(*it);
+    }
+    if (total + (int64_t)fl.size() > ctx->sched_cap) break;
+    for (const abft_flip& f : fl) {
+      DevFlip& d = ctx->h_flips[total++];
+      d.step = f.step; d.grid = f.grid; d.z = f.z; d.y = f.y; d.x = f.x; d.bit = f.bit; d.target = f.target;
+    }
+    ctx->h_off[t - t0 + 1] = (int)total;
+  }
+  if (t == t0 && n > 0) return fail(ctx, ABFT_E_INVAL, "flips of one sweep exceed the schedule capacity");
+  *covered = t - t0;
+  ctx->flips_scheduled += total;
+  if (total) CK(cudaMemcpyAsync(ctx->d_flips, ctx->h_flips, sizeof(DevFlip) * total, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_off, ctx->h_off, sizeof(int) * (*covered + 1), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->h_ctrl->sched_t0 = t0;
+  ctx->h_ctrl->sched_n = (int)*covered;
+  CK(cudaMemcpyAsync(&ctx->ctrl->sched_t0, &ctx->h_ctrl->sched_t0, sizeof(long long) + sizeof(int),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  ctx->sched_live = true;
+  return ABFT_OK;
+}
+
+abft_status set_inject_enabled(abft_ctx* ctx, int on) {
+  ctx->h_ctrl->inject_enabled = on;
+  CK(cudaMemcpyAsync(&ctx->ctrl->inject_enabled, &ctx->h_ctrl->inject_enabled, sizeof(int),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  return ABFT_OK;
+}
+
+abft_status read_ctrl(abft_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_ctrl, ctx->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_gctrl, ctx->gctrl, sizeof(DevGridCtrl) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ABFT_OK;
+}
+
+// make A[cur], B[cur] the checksums of the current state (trusted, Theorem 2's premise)
+abft_status ensure_checksums(abft_ctx* ctx, int gi) {
+  if (ctx->ck_valid[gi]) return ABFT_OK;
+  const GridDev& g = ctx->g[gi];
+  const int c = ctx->cur[gi];
+  const Launch L = launcher(ctx);
+  CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.A[c], g.B[c]); }));
+  ctx->ck_valid[gi] = 1;
+  return ABFT_OK;
+}
+
+// one sweep of every grid; protected sweeps write partial checksums
+abft_status sweep_all(abft_ctx* ctx, int mode) {
+  const Launch L = launcher(ctx);
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    const GridDev& g = ctx->g[gi];
+    const int in = ctx->cur[gi];
+    if (mode == ABFT_MODE_ONLINE) {
+      const int out = (in + 1) % 3;  // the verified state moves with every sweep
+      CK(run(ctx, kKSweepProt, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
+      CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(L, g, in, out); }));
+      ctx->cur[gi] = out;
+      ctx->ref[gi] = out;
+      ctx->ref_step[gi] = ctx->step + 1;
+      ctx->ck_valid[gi] = 1;
+    } else {
+      const int out = other_than(in, ctx->ref[gi]);
+      CK(run(ctx, kKSweepPlain, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, false); }));
+      ctx->cur[gi] = out;
+      ctx->ck_valid[gi] = 0;
+    }
+  }
+  ++ctx->step;
+  return ABFT_OK;
+}
+
+abft_status status_from_device(abft_ctx* ctx) {
+  const unsigned st = ctx->h_ctrl->status;
+  ctx->status_seen |= st;
+  if (st & kStTimeout) return fail(ctx, ABFT_E_TIMEOUT, "a device-side wait timed out");
+  if (st & kStFlipOverflow) return fail(ctx, ABFT_E_INVAL, "more than %d flips in one tile and sweep", kLocalFlips);
+  if (st & kStEventOverflow) return fail(ctx, ABFT_E_TRUNCATED, "event log overflow (capacity %d)", ctx->opt.event_capacity);
+  return ABFT_OK;
+}
+
+// host-side event append (rollbacks): stream-ordered copies from pinned staging
+abft_status host_event(abft_ctx* ctx, int64_t step, int grid, int kind, float before, float after) {
+  abft_status s = read_ctrl(ctx);
+  if (s) return s;
+  const unsigned long long i = ctx->h_ctrl->ev_count;
+  if (i < (unsigned long long)ctx->opt.event_capacity) {
+    abft_event* e = ctx->h_ev;
+    memset(e, 0, sizeof *e);
+    e->step = step; e->grid = grid; e->z = -1; e->y = -1; e->x = -1; e->kind = kind;
+    e->before = before; e->after = after;
+    CK(cudaMemcpyAsync(ctx->events + i, e, sizeof *e, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    ctx->h_ctrl->status |= kStEventOverflow;
+    CK(cudaMemcpyAsync(&ctx->ctrl->status, &ctx->h_ctrl->status, sizeof(unsigned), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
+  ctx->h_ctrl->ev_count = i + 1;
+  CK(cudaMemcpyAsync(&ctx->ctrl->ev_count, &ctx->h_ctrl->ev_count, sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ABFT_OK;
+}
+
+abft_status set_grid_step(abft_ctx* ctx, int gi, int64_t step) {
+  ctx->h_gctrl[gi].step = step;
+  CK(cudaMemcpyAsync(&ctx->gctrl[gi].step, &ctx->h_gctrl[gi].step, sizeof(long long), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  return ABFT_OK;
+}
+
+abft_status clear_verdicts(abft_ctx* ctx) {
+  for (int gi = 0; gi < ctx->n; ++gi)
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].verdict, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  return ABFT_OK;
+}
+
+// chain Theorem 1 d times from (a0, b0); returns the index of the AP/BP slot holding the result
+abft_status chain(abft_ctx* ctx, int gi, const double* a0, const double* b0, int64_t d, int* slot) {
+  const GridDev& g = ctx->g[gi];
+  const Launch L = launcher(ctx);
+  const double* a = a0;
+  const double* b = b0;
+  int s = 0;
+  for (int64_t k = 0; k < d; ++k) {
+    s = (int)(k & 1);
+    CK(run(ctx, kKChain, [&] { return launch_chain(L, g, a, b, g.AP[s], g.BP[s]); }));
+    a = g.AP[s];
+    b = g.BP[s];
+  }
+  *slot = s;
+  return ABFT_OK;
+}
+
+// one offline window of d sweeps (Sec. 4): checkpoint, sweep, chain, compare, roll back
+abft_status offline_window(abft_ctx* ctx, int64_t d) {
+  const Launch L = launcher(ctx);
+  const int64_t t_start = ctx->step;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    abft_status s = ensure_checksums(ctx, gi);
+    if (s) return s;
+    ctx->ref[gi] = ctx->cur[gi];  // the checkpoint is the retained buffer itself
+    ctx->ref_step[gi] = t_start;
+  }
+  abft_status s = clear_verdicts(ctx);
+  if (s) return s;
+  auto run_window = [&](const std::vector<int>& which) -> abft_status {
+    for (int64_t k = 0; k < d; ++k) {
+      for (int gi : which) {
+        const GridDev& g = ctx->g[gi];
+        const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
+        const bool last = k == d - 1;
+        CK(run(ctx, last ? kKSweepProt : kKSweepPlain,
+               [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, last); }));
+        ctx->cur[gi] = out;
+      }
+    }
+    for (int gi : which) {
+      const GridDev& g = ctx->g[gi];
+      const int c = ctx->cur[gi];
+      CK(run(ctx, kKCheckOffline, [&] { return launch_reduce_partials(L, g, c); }));
+      const int slot = (int)((d - 1) & 1);
+      CK(run(ctx, kKCheckOffline, [&] { return launch_compare(L, g, g.AP[slot], g.BP[slot], g.A[c], g.B[c]); }));
+    }
+    return ABFT_OK;
+  };
+  std::vector<int> all(ctx->n);
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    all[gi] = gi;
+    int slot;
+    s = chain(ctx, gi, ctx->g[gi].A[ctx->ref[gi]], ctx->g[gi].B[ctx->ref[gi]], d, &slot);
+    if (s) return s;
+  }
+  s = run_window(all);
+  if (s) return s;
+  s = read_ctrl(ctx);
+  if (s) return s;
+  std::vector<int> bad;
+  for (int gi = 0; gi < ctx->n; ++gi)
+    if (ctx->h_gctrl[gi].verdict) bad.push_back(gi);
+  if (!bad.empty()) {  // Sec. 4.2: restore the checkpoint and recompute, without injection
+    for (int gi : bad) {
+      s = host_event(ctx, t_start, gi, ABFT_EV_ROLLBACK, (float)ctx->h_gctrl[gi].verdict, (float)d);
+      if (s) return s;
+      s = set_grid_step(ctx, gi, t_start);
+      if (s) return s;
+      ctx->cur[gi] = ctx->ref[gi];
+      ++ctx->rollbacks;
+    }
+    s = clear_verdicts(ctx);
+    if (s) return s;
+    s = set_inject_enabled(ctx, 0);
+    if (s) return s;
+    s = run_window(bad);
+    if (s) return s;
+    s = set_inject_enabled(ctx, 1);
+    if (s) return s;
+    s = read_ctrl(ctx);
+    if (s) return s;
+    for (int gi : bad)
+      if (ctx->h_gctrl[gi].verdict)
+        return fail(ctx, ABFT_E_UNCORRECTABLE, "grid %d: recomputed window from step %lld still mismatches", gi,
+                    (long long)t_start);
+  }
+  ctx->step = t_start + d;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    ctx->ref[gi] = ctx->cur[gi];
+    ctx->ref_step[gi] = ctx->step;
+    ctx->ck_valid[gi] = 1;
+  }
+  return ABFT_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+
+extern "C" {
+
+void abft_default_options(abft_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->eps = 1e-5;
+  o->delta = 16;
+  o->acc = ABFT_ACC_FP32;
+  o->event_capacity = 4096;
+  o->graph_steps = 50;
+  o->tile_y = 0;
+  o->max_flips_per_step = 64;
+  o->stream = nullptr;
+}
+
+size_t abft_workspace_bytes(const abft_grid* grids, int32_t n_grids, const abft_options* opt) {
+  if (!opt) return 0;
+  Plan P;
+  if (!make_plan(grids, n_grids, *opt, &P)) return 0;
+  return P.total;
+}
+
+const char* abft_status_string(abft_status s) {
+  switch (s) {
+    case ABFT_OK: return "ok";
+    case ABFT_E_INVAL: return "invalid argument";
+    case ABFT_E_CUDA: return "CUDA error";
+    case ABFT_E_NOMEM: return "workspace too small";
+    case ABFT_E_STATE: return "invalid state";
+    case ABFT_E_TIMEOUT: return "device wait timed out";
+    case ABFT_E_UNCORRECTABLE: return "uncorrectable mismatch";
+    case ABFT_E_TRUNCATED: return "event log truncated";
+  }
+  return "unknown status";
+}
+
+const char* abft_last_error(const abft_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t abft_schedule(uint64_t seed, double rate, uint32_t bitmask, int32_t grid, int32_t n_grids, int32_t nx,
+                      int32_t ny, int32_t nz, int64_t t_begin, int64_t t_end, abft_flip* out, int64_t cap) {
+  const abft_grid G{nx, ny, nz};
+  if (!valid_grid(G) || n_grids < 1 || grid < 0 || grid >= n_grids || t_begin < 0 || t_end < t_begin ||
+      !(rate >= 0) || !std::isfinite(rate) || cap < 0 || (cap > 0 && !out))
+    return -1;
+  std::vector<abft_flip> fl;
+  int64_t n = 0;
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    fl.clear();
+    seeded_flips(seed, rate, bitmask, grid, n_grids, G, t, &fl);
+    for (const abft_flip& f : fl) {
+      if (n < cap) out[n] = f;
+      ++n;
+    }
+  }
+  return n;
+}
+
+void abft_destroy(abft_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->h_flips) cudaFreeHost(ctx->h_flips);
+  if (ctx->h_off) cudaFreeHost(ctx->h_off);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  if (ctx->h_gctrl) cudaFreeHost(ctx->h_gctrl);
+  if (ctx->h_ev) cudaFreeHost(ctx->h_ev);
+  delete ctx;
+}
+
+abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, const float* const* temp,
+                      const float* const* power, const abft_coeffs* coeffs, const abft_options* opt,
+                      void* workspace, size_t workspace_bytes) {
+  if (!out) return ABFT_E_INVAL;
+  *out = nullptr;
+  if (!grids || n_grids < 1 || !temp || !power || !coeffs || !opt || !workspace) return ABFT_E_INVAL;
+  if (((uintptr_t)workspace & 255) != 0) return ABFT_E_INVAL;
+  Plan P;
+  if (!make_plan(grids, n_grids, *opt, &P)) return ABFT_E_INVAL;
+  if (workspace_bytes < P.total) return ABFT_E_NOMEM;
+  for (int i = 0; i < n_grids; ++i)
+    if (!temp[i] || !power[i]) return ABFT_E_INVAL;
+
+  abft_ctx* ctx = new (std::nothrow) abft_ctx;
+  if (!ctx) return ABFT_E_NOMEM;
+  abft_status st = ABFT_OK;
+  auto bail = [&](abft_status s) {
+    abft_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(ABFT_E_CUDA);
+  ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)opt->stream;
+  ctx->n = n_grids;
+  ctx->grids.assign(grids, grids + n_grids);
+  ctx->co.assign(coeffs, coeffs + n_grids);
+  char* ws = (char*)workspace;
+  const int ty = pick_ty(*opt);
+  ctx->g.resize(n_grids);
+  ctx->ctrl = (DevCtrl*)(ws + P.ctrl);
+  ctx->gctrl = (DevGridCtrl*)(ws + P.gctrl);
+  ctx->events = (abft_event*)(ws + P.events);
+  ctx->d_flips = (DevFlip*)(ws + P.flips);
+  ctx->d_off = (int*)(ws + P.off);
+  ctx->sched_cap = P.sched_cap;
+  if (cudaMallocHost(&ctx->h_flips, sizeof(DevFlip) * P.sched_cap) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_off, sizeof(int) * (kSchedSteps + 1)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_gctrl, sizeof(DevGridCtrl) * n_grids) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_ev, sizeof(abft_event)) != cudaSuccess)
+    return bail(ABFT_E_NOMEM);
+  memset(ctx->h_ctrl, 0, sizeof(DevCtrl));
+  memset(ctx->h_gctrl, 0, sizeof(DevGridCtrl) * n_grids);
+  for (int i = 0; i < n_grids; ++i) {
+    const abft_grid& G = grids[i];
+    const GridPlan& p = P.g[i];
+    GridDev& g = ctx->g[i];
+    memset(&g, 0, sizeof g);
+    g.nx = G.nx; g.ny = G.ny; g.nz = G.nz;
+    g.px = (int)align_up(G.nx, 32);
+    g.ty = ty;
+    g.ntx = (G.nx + kTX - 1) / kTX;
+    g.nty = (G.ny + ty - 1) / ty;
+    g.pa_stride = g.ntx * kTX;
+    g.acc = opt->acc;
+    g.gid = i;
+    g.eps = opt->eps;
+    const abft_coeffs& c = coeffs[i];
+    g.k = Coef{c.cc, c.cw, c.ce, c.cn, c.cs, c.cb, c.ct};
+    for (int k = 0; k < 3; ++k) {
+      g.u[k] = (float*)(ws + p.u[k]);
+      g.A[k] = (double*)(ws + p.A[k]);
+      g.B[k] = (double*)(ws + p.B[k]);
+      g.AP[k] = (double*)(ws + p.AP[k]);
+      g.BP[k] = (double*)(ws + p.BP[k]);
+    }
+    g.C = (float*)(ws + p.C);
+    g.cx = (double*)(ws + p.cx);
+    g.cy = (double*)(ws + p.cy);
+    g.PA = ws + p.PA;
+    g.PB = ws + p.PB;
+    g.fcnt = (int*)(ws + p.fcnt);
+    g.fidx = (int*)(ws + p.fidx);
+    g.gc = ctx->gctrl + i;
+  }
+  ctx->tm_u.resize(3 * n_grids);
+  ctx->tm_c.resize(n_grids);
+  ctx->cur.assign(n_grids, 0);
+  ctx->ref.assign(n_grids, 0);
+  ctx->ref_step.assign(n_grids, 0);
+  ctx->ck_valid.assign(n_grids, 1);
+  cudaStream_t s = ctx->stream;
+#define CKI(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      st = fail(ctx, ABFT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                    \
+      fprintf(stderr, "abft_init: %s\n", ctx->err.c_str());                                    \
+      return bail(st);                                                                         \
+    }                                                                                          \
+  } while (0)
+  CKI(cudaMemsetAsync(workspace, 0, P.total, s));
+  const Launch L = launcher(ctx);
+  for (int i = 0; i < n_grids; ++i) {
+    GridDev& g = ctx->g[i];
+    const size_t rows = (size_t)g.ny * g.nz;
+    CKI(cudaMemcpy2DAsync(g.u[0], g.px * 4, temp[i], (size_t)g.nx * 4, (size_t)g.nx * 4, rows, cudaMemcpyDefault, s));
+    CKI(cudaMemcpy2DAsync(g.C, g.px * 4, power[i], (size_t)g.nx * 4, (size_t)g.nx * 4, rows, cudaMemcpyDefault, s));
+    CKI(run(ctx, kKOther, [&] { return launch_source_term(L, g, coeffs[i]); }));
+    CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.C, g.cx, g.cy); }));
+    CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[0], g.A[0], g.B[0]); }));
+    char e[256];
+    if (make_tensor_maps(g, ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess) {
+      st = fail(ctx, ABFT_E_CUDA, "%s", e);
+      return bail(st);
+    }
+  }
+  ctx->h_ctrl->ev_cap = opt->event_capacity;
+  ctx->h_ctrl->inject_enabled = 1;
+  CKI(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, s));
+  CKI(cudaStreamSynchronize(s));
+#undef CKI
+  *out = ctx;
+  return ABFT_OK;
+}
+
+abft_status abft_inject(abft_ctx* ctx, uint64_t seed, double rate, uint32_t bitmask) {
+  if (!ctx) return ABFT_E_INVAL;
+  if (!(rate >= 0) || !std::isfinite(rate)) return fail(ctx, ABFT_E_INVAL, "rate must be finite and >= 0");
+  if (rate > ctx->opt.max_flips_per_step) return fail(ctx, ABFT_E_INVAL, "rate above max_flips_per_step");
+  ctx->inj_kind = (rate > 0 && bitmask) ? 1 : 0;
+  ctx->seed = seed;
+  ctx->rate = rate;
+  ctx->mask = bitmask;
+  ctx->list.clear();
+  return ABFT_OK;
+}
+
+abft_status abft_inject_list(abft_ctx* ctx, const abft_flip* flips, int64_t n) {
+  if (!ctx || n < 0 || (n > 0 && !flips)) return ABFT_E_INVAL;
+  std::vector<abft_flip> v(flips, flips + n);
+  for (const abft_flip& f : v) {
+    if (f.grid < 0 || f.grid >= ctx->n || f.step < 0 || f.bit < 0 || f.bit > 31 || f.target != 0)
+      return fail(ctx, ABFT_E_INVAL, "invalid flip entry");
+    const abft_grid& G = ctx->grids[f.grid];
+    if (f.x < 0 || f.x >= G.nx || f.y < 0 || f.y >= G.ny || f.z < 0 || f.z >= G.nz)
+      return fail(ctx, ABFT_E_INVAL, "flip outside grid %d", f.grid);
+  }
+  std::stable_sort(v.begin(), v.end(), [](const abft_flip& a, const abft_flip& b) {
+    return a.step < b.step || (a.step == b.step && a.grid < b.grid);
+  });
+  ctx->list.swap(v);
+  ctx->inj_kind = ctx->list.empty() ? 0 : 2;
+  return ABFT_OK;
+}
+
+abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
+  if (!ctx) return ABFT_E_INVAL;
+  if (n < 0 || mode < 0 || mode > 2) return fail(ctx, ABFT_E_INVAL, "bad step count or mode");
+  if (ctx->status_seen & kStTimeout) return fail(ctx, ABFT_E_TIMEOUT, "context poisoned by an earlier timeout");
+  if (mode == ABFT_MODE_OFFLINE)
+    for (int gi = 0; gi < ctx->n; ++gi)
+      if (!offline_capable(ctx->co[gi]))
+        return fail(ctx, ABFT_E_INVAL, "offline mode needs cn == cs and cw == ce (grid %d)", gi);
+  ctx->verified = false;
+  const int64_t t_end = ctx->step + n;
+  abft_status s = ABFT_OK;
+  while (ctx->step < t_end) {
+    int64_t want = std::min<int64_t>(t_end - ctx->step, kSchedSteps);
+    if (mode == ABFT_MODE_OFFLINE) want = std::min<int64_t>(want, std::max<int64_t>(ctx->opt.delta, 1));
+    int64_t covered = 0;
+    s = upload_schedule(ctx, ctx->step, want, &covered);
+    if (s) return s;
+    if (mode == ABFT_MODE_OFFLINE) {
+      s = offline_window(ctx, covered);
+      if (s) return s;
+      continue;
+    }
+    for (int64_t k = 0; k < covered; ++k) {
+      if (mode == ABFT_MODE_ONLINE)
+        for (int gi = 0; gi < ctx->n; ++gi) {
+          s = ensure_checksums(ctx, gi);
+          if (s) return s;
+        }
+      s = sweep_all(ctx, mode);
+      if (s) return s;
+    }
+  }
+  s = read_ctrl(ctx);
+  if (s) return s;
+  return status_from_device(ctx);
+}
+
+abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
+  if (!ctx || !n_mismatch) return ABFT_E_INVAL;
+  const Launch L = launcher(ctx);
+  abft_status s = clear_verdicts(ctx);
+  if (s) return s;
+  ctx->v_dist.assign(ctx->n, 0);
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    const GridDev& g = ctx->g[gi];
+    const int c = ctx->cur[gi], r = ctx->ref[gi];
+    const int64_t d = ctx->step - ctx->ref_step[gi];
+    ctx->v_dist[gi] = d;
+    if (d > 0 && !offline_capable(ctx->co[gi]))
+      return fail(ctx, ABFT_E_INVAL, "chained verification needs cn == cs and cw == ce (grid %d)", gi);
+    CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.AP[2], g.BP[2]); }));
+    const double* pa = g.A[r];
+    const double* pb = g.B[r];
+    if (d > 0) {
+      int slot;
+      s = chain(ctx, gi, g.A[r], g.B[r], d, &slot);
+      if (s) return s;
+      pa = g.AP[slot];
+      pb = g.BP[slot];
+    }
+    CK(run(ctx, kKCheckOffline, [&] { return launch_compare(L, g, pa, pb, g.AP[2], g.BP[2]); }));
+  }
+  s = read_ctrl(ctx);
+  if (s) return s;
+  int64_t tot = 0;
+  ctx->v_fail.assign(ctx->n, 0);
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    ctx->v_fail[gi] = ctx->h_gctrl[gi].verdict;
+    tot += (int64_t)ctx->h_gctrl[gi].verdict;
+  }
+  ctx->verified = true;
+  *n_mismatch = tot;
+  return status_from_device(ctx);
+}
+
+abft_status abft_correct(abft_ctx* ctx, int64_t* n_fixed) {
+  if (!ctx || !n_fixed) return ABFT_E_INVAL;
+  if (!ctx->verified) return fail(ctx, ABFT_E_STATE, "abft_correct needs a preceding abft_verify");
+  const Launch L = launcher(ctx);
+  *n_fixed = 0;
+  abft_status s = ABFT_OK;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    if (!ctx->v_fail[gi]) continue;
+    const GridDev& g = ctx->g[gi];
+    const int64_t d = ctx->v_dist[gi];
+    if (d == 0) {  // Eq. (8) against the stored checksums of this very state
+      const int c = ctx->cur[gi];
+      CK(cudaMemsetAsync(&ctx->gctrl[gi].unresolved, 0, sizeof(unsigned long long), ctx->stream));
+      CK(run(ctx, kKOther, [&] { return launch_correct_planes(L, g, c, g.A[c], g.B[c]); }));
+      s = read_ctrl(ctx);
+      if (s) return s;
+      if (ctx->h_gctrl[gi].unresolved)
+        return fail(ctx, ABFT_E_UNCORRECTABLE, "grid %d: mismatch pattern cannot be located", gi);
+      *n_fixed += (int64_t)ctx->v_fail[gi] / 2;
+    } else {  // Sec. 4.2: roll back to the verified state and recompute d sweeps
+      CK(cudaStreamSynchronize(ctx->stream));
+      s = set_grid_step(ctx, gi, ctx->ref_step[gi]);
+      if (s) return s;
+      s = host_event(ctx, ctx->ref_step[gi], gi, ABFT_EV_ROLLBACK, (float)ctx->v_fail[gi], (float)d);
+      if (s) return s;
+      s = set_inject_enabled(ctx, 0);
+      if (s) return s;
+      ctx->cur[gi] = ctx->ref[gi];
+      for (int64_t k = 0; k < d; ++k) {
+        const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
+        CK(run(ctx, kKSweepPlain, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, false); }));
+        ctx->cur[gi] = out;
+      }
+      s = set_inject_enabled(ctx, 1);
+      if (s) return s;
+      ++ctx->rollbacks;
+      *n_fixed += d;
+    }
+    ctx->ck_valid[gi] = 0;
+  }
+  ctx->verified = false;
+  s = read_ctrl(ctx);
+  if (s) return s;
+  return status_from_device(ctx);
+}
+
+abft_status abft_events(abft_ctx* ctx, abft_event* buf, int64_t cap, int64_t* n_out) {
+  if (!ctx || !n_out || cap < 0 || (cap > 0 && !buf)) return ABFT_E_INVAL;
+  abft_status s = read_ctrl(ctx);
+  if (s) return s;
+  const int64_t n = (int64_t)ctx->h_ctrl->ev_count;
+  const int64_t kept = std::min<int64_t>(n, ctx->opt.event_capacity);
+  const int64_t m = std::min<int64_t>(kept, cap);
+  if (m > 0) CK(cudaMemcpy(buf, ctx->events, sizeof(abft_event) * m, cudaMemcpyDeviceToHost));
+  *n_out = n;
+  return n > ctx->opt.event_capacity ? fail(ctx, ABFT_E_TRUNCATED, "event log overflow") : ABFT_OK;
+}
+
+abft_status abft_read(abft_ctx* ctx, int32_t grid, float* dst) {
+  if (!ctx || !dst || grid < 0 || grid >= ctx->n) return ABFT_E_INVAL;
+  const GridDev& g = ctx->g[grid];
+  CK(cudaMemcpy2DAsync(dst, (size_t)g.nx * 4, g.u[ctx->cur[grid]], (size_t)g.px * 4, (size_t)g.nx * 4,
+                       (size_t)g.ny * g.nz, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ABFT_OK;
+}
+
+abft_status abft_current(abft_ctx* ctx, int32_t grid, float** dev_ptr, int64_t* pitch) {
+  if (!ctx || !dev_ptr || !pitch || grid < 0 || grid >= ctx->n) return ABFT_E_INVAL;
+  *dev_ptr = ctx->g[grid].u[ctx->cur[grid]];
+  *pitch = ctx->g[grid].px;
+  return ABFT_OK;
+}
+
+abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out) {
+  if (!ctx || !out) return ABFT_E_INVAL;
+  out->steps_done = ctx->step;
+  out->kernel_launches = ctx->launches;
+  out->events = (int64_t)ctx->h_ctrl->ev_count;
+  out->rollbacks = ctx->rollbacks;
+  out->flips_scheduled = ctx->flips_scheduled;
+  return ABFT_OK;
+}
+
+abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return ABFT_E_INVAL;
+  for (int k = 0; k < ABFT_KERNEL_KINDS; ++k) { ms[k] = 0; launches[k] = 0; }
+  ctx->timing = true;
+  ctx->ev_used = 0;
+  ctx->ev_kind.clear();
+  abft_status s = abft_step(ctx, n, mode);
+  ctx->timing = false;
+  if (s != ABFT_OK && s != ABFT_E_TRUNCATED) return s;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (size_t i = 0; i < ctx->ev_kind.size(); ++i) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]));
+    ms[ctx->ev_kind[i]] += t;
+    launches[ctx->ev_kind[i]] += 1;
+  }
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units (host + device).
+// Not part of the public ABI; see include/abft.h for that.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "abft.h"
+
+namespace abft {
+
+constexpr int kTX = 128;          // sweep tile width: one warp, one float4 per lane
+constexpr int kHaloX = 4;         // x halo of a TMA tile (16-byte aligned start)
+constexpr int kUW = kTX + 2 * kHaloX;  // width of the staged u tile
+constexpr int kFCap = 64;         // failing entries kept per plane and vector
+constexpr int kLocalFlips = 32;   // flips a tile can apply in one sweep
+constexpr int kSchedSteps = 4096; // sweeps covered by one uploaded schedule chunk
+constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side wait loop
+
+// sticky device status bits
+enum : unsigned {
+  kStTimeout = 1u,        // a TMA/mbarrier wait gave up
+  kStFlipOverflow = 2u,   // more flips in one tile and sweep than kLocalFlips
+  kStEventOverflow = 4u,  // event log full
+  kStFailOverflow = 8u    // more failing entries in a plane than kFCap (plane recomputed)
+};
+
+// kernel kinds for launch accounting and abft_time_kernels
+enum KernelKind { kKSweepPlain = 0, kKSweepProt = 1, kKCheckOnline = 2, kKCheckOffline = 3,
+                  kKChain = 4, kKOther = 5 };
+
+struct Coef {
+  float cc, cw, ce, cn, cs, cb, ct;
+};
+
+// device-resident control block of a context
+struct DevCtrl {
+  unsigned int status;
+  int inject_enabled;
+  long long sched_t0;       // sweep index of schedule offset 0
+  int sched_n;              // sweeps covered by the uploaded schedule
+  int ev_cap;
+  unsigned long long ev_count;
+  unsigned long long verdict;  // failing entries found by the last offline/verify check
+};
+
+// per-grid device counters
+struct DevGridCtrl {
+  long long step;           // sweeps committed on this grid
+  unsigned int done_sweep;  // last-block tickets
+  unsigned int done_check;
+  unsigned int done_aux;
+  unsigned int pad;
+  unsigned long long verdict;  // failing entries of the last offline/verify comparison
+  unsigned long long unresolved;  // planes a zero-distance correction could not fix
+};
+
+// everything a kernel needs to know about one grid (passed by value)
+struct GridDev {
+  int nx, ny, nz, px;       // px: row pitch in elements (multiple of 32)
+  int ntx, nty, ty;         // sweep tiles along x and y, rows per tile
+  int pa_stride;            // row stride of the a-partials (ntx * kTX)
+  int acc;                  // abft_acc
+  int gid;
+  Coef k;
+  double eps;
+  float* u[3];              // state buffers
+  float* C;                 // constant term, same pitch
+  double* cx; double* cy;   // checksums of C (Theorem 1's c_x, c_y)
+  double* A[3]; double* B[3];  // checksums of the state held in u[i]
+  double* AP[3]; double* BP[3];  // interpolated vectors (prediction, chain ping-pong, fresh sums)
+  void* PA; void* PB;       // per-tile partial checksums of the last protected sweep
+  int* fcnt;                // [nz][2] failing-entry counts (a, b)
+  int* fidx;                // [nz][2][kFCap] failing indices
+  DevGridCtrl* gc;
+};
+
+// device flip entry (same layout as abft_flip)
+struct DevFlip { long long step; int grid, z, y, x, bit, target; };
+
+struct DevSched {
+  const DevFlip* flips;
+  const int* off;           // off[i]..off[i+1]: flips of sweep sched_t0 + i (all grids)
+};
+
+// host-side launchers (defined in sweep.cu / check.cu); all enqueue on `s`
+struct Launch {
+  cudaStream_t s;
+  DevCtrl* ctrl;
+  abft_event* events;
+  DevSched sched;
+};
+
+cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUtensorMap* tm_c,
+                             char* err, size_t errlen);
+int sweep_smem_bytes(int ty, bool prot);
+cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
+                         const CUtensorMap& tm_c, int in, int out, bool prot);
+cudaError_t launch_source_term(const Launch& L, const GridDev& g, const abft_coeffs& co);
+cudaError_t launch_checksums(const Launch& L, const GridDev& g, const float* u, double* A, double* B);
+cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out);
+cudaError_t launch_reduce_partials(const Launch& L, const GridDev& g, int out);
+cudaError_t launch_chain(const Launch& L, const GridDev& g, const double* a_in, const double* b_in,
+                         double* a_out, double* b_out);
+cudaError_t launch_compare(const Launch& L, const GridDev& g, const double* ap, const double* bp,
+                           const double* a, const double* b);
+cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
+                                  const double* bp);
+
+}  // namespace abft

@@ -1,0 +1,164 @@
+// Device helpers: the Eq. (1) point update, reductions, mbarrier and TMA wrappers.
+#pragma once
+
+#include "abft_internal.h"
+
+namespace abft {
+
+// Eq. (1) for the 7-point HotSpot3D set: C + cc*c + cw*w + ce*e + cn*n + cs*s + cb*b + ct*t.
+// One fixed chain of fused multiply-adds, used by the sweep and by every recomputation,
+// so that a recomputed point is bit-identical to the swept one.
+__device__ __forceinline__ float hs_update(const Coef& k, float c, float w, float e, float n,
+                                           float s, float b, float t, float C) {
+  float v = __fmaf_rn(k.cc, c, C);
+  v = __fmaf_rn(k.cw, w, v);
+  v = __fmaf_rn(k.ce, e, v);
+  v = __fmaf_rn(k.cn, n, v);
+  v = __fmaf_rn(k.cs, s, v);
+  v = __fmaf_rn(k.cb, b, v);
+  v = __fmaf_rn(k.ct, t, v);
+  return v;
+}
+
+// Eq. (1) at one point read straight from global memory, neighbours clamped (Fig. 2).
+__device__ __forceinline__ float point_update(const GridDev& g, const float* __restrict__ u,
+                                              int z, int y, int x) {
+  const size_t plane = (size_t)g.ny * g.px;
+  const float* p = u + (size_t)z * plane + (size_t)y * g.px + x;
+  const float c = p[0];
+  const float w = x > 0 ? p[-1] : c;
+  const float e = x < g.nx - 1 ? p[1] : c;
+  const float n = y > 0 ? p[-g.px] : c;
+  const float s = y < g.ny - 1 ? p[g.px] : c;
+  const float b = z > 0 ? p[-(ptrdiff_t)plane] : c;
+  const float t = z < g.nz - 1 ? p[plane] : c;
+  const float C = g.C[(size_t)z * plane + (size_t)y * g.px + x];
+  return hs_update(g.k, c, w, e, n, s, b, t, C);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// compensated accumulation of v into (hi, lo)
+__device__ __forceinline__ void acc2(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  hi = s;
+  lo += e;
+}
+
+__device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h, s, e);
+    hi = s;
+    lo = lo + l + e;
+  }
+}
+
+// block-wide FP64 sum (deterministic; every thread gets the result); `red` holds 32 doubles
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__device__ __forceinline__ void set_status(DevCtrl* c, unsigned bits) { atomicOr(&c->status, bits); }
+
+__device__ __forceinline__ void log_event(DevCtrl* c, abft_event* ev, long long step, int grid, int z,
+                                          int y, int x, int kind, float before, float after) {
+  const unsigned long long i = atomicAdd(&c->ev_count, 1ull);
+  if (i < (unsigned long long)c->ev_cap) {
+    abft_event e;
+    e.step = step; e.grid = grid; e.z = z; e.y = y; e.x = x; e.kind = kind;
+    e.before = before; e.after = after;
+    ev[i] = e;
+  } else {
+    set_status(c, kStEventOverflow);
+  }
+}
+
+// ---------------------------------------------------------------- mbarrier / TMA
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Wait for phase `parity` of the barrier to complete; gives up after kSpinLimit polls
+// and reports it through the status word instead of hanging.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, DevCtrl* ctrl) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  set_status(ctrl, kStTimeout);
+  return false;
+}
+
+// 3D tiled TMA load of one box into shared memory, completion on `bar`
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
+}  // namespace abft

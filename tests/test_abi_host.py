@@ -1,0 +1,105 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+symbol include/abft.h declares, validates arguments, and its seeded flip schedule
+equals the oracle's independent SplitMix64 implementation."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def abi():
+    from paper_1909_00709_gb300 import abi, build
+    build.build()
+    abi.lib()
+    return abi
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^ABFT_API[^(]*?\b(abft_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(abi):
+    names = declared_symbols()
+    assert len(names) >= 17
+    L = abi.lib()
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(abi.EXPORTS) <= names
+
+
+def test_struct_layouts_match_numpy_views(abi):
+    assert ct.sizeof(abi.abft_event) == abi.EVENT.itemsize == 40
+    assert ct.sizeof(abi.abft_flip) == abi.FLIP.itemsize == 32
+    for name, off in abi.EVENT.fields.items():
+        assert getattr(abi.abft_event, name).offset == off[1]
+    for name, off in abi.FLIP.fields.items():
+        assert getattr(abi.abft_flip, name).offset == off[1]
+
+
+def test_default_options_follow_table1(abi):
+    o = abi.abft_default_options()
+    assert o.eps == 1e-5 and o.delta == 16
+    assert o.event_capacity > 0 and o.max_flips_per_step > 0
+
+
+def test_workspace_bytes_validates(abi):
+    o = abi.abft_default_options()
+    assert abi.abft_workspace_bytes([(64, 64, 8)], o) > 3 * 64 * 64 * 8 * 4
+    assert abi.abft_workspace_bytes([(0, 64, 8)], o) == 0
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(tile_y=12)) == 0
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(eps=-1.0)) == 0
+    big = abi.abft_workspace_bytes([(1024, 1024, 256)], o)
+    assert big > 4 * 1024 * 1024 * 256 * 4
+    two = abi.abft_workspace_bytes([(64, 64, 8), (100, 37, 5)], o)
+    assert two > abi.abft_workspace_bytes([(64, 64, 8)], o)
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(abi):
+    L = abi.lib()
+    h = ct.c_void_p()
+    g = (abi.abft_grid * 1)(abi.abft_grid(8, 8, 2))
+    o = abi.abft_default_options()
+    # NULL pointers and misaligned workspaces are refused before any CUDA call
+    assert L.abft_init(ct.byref(h), g, 1, None, None, None, ct.byref(o), None, 0) == 1
+    tp = (ct.c_void_p * 1)(1024)
+    co = (abi.abft_coeffs * 1)()
+    assert L.abft_init(ct.byref(h), g, 1, tp, tp, co, ct.byref(o), ct.c_void_p(0x1001), 1 << 30) == 1
+    assert L.abft_init(ct.byref(h), g, 1, tp, tp, co, ct.byref(o), ct.c_void_p(0x1000), 16) == 3
+
+
+@pytest.mark.parametrize("rate,mask,shape,n_grids,grid", [
+    (1e-3, 0xFFFFFFFF, (512, 512, 8), 1, 0),
+    (0.25, 0xFFFFFFFF, (64, 64, 8), 1, 0),
+    (3.7, 0x0000FF00, (100, 37, 5), 4, 2),
+    (268.435456, 0xFFFFFFFF, (1024, 1024, 256), 1, 0),
+])
+def test_schedule_matches_oracle_generator(abi, orc, rate, mask, shape, n_grids, grid):
+    steps = 200 if rate > 100 else 2000
+    lib_s = abi.abft_schedule(12345, rate, mask, shape, 0, steps, grid=grid, n_grids=n_grids)
+    orc_s = orc.schedule(12345, rate, mask, shape, 0, steps, grid=grid, n_grids=n_grids)
+    assert len(lib_s) == len(orc_s)
+    for f in ("step", "grid", "z", "y", "x", "bit"):
+        np.testing.assert_array_equal(lib_s[f], orc_s[f])
+
+
+def test_schedule_rejects_bad_arguments(abi):
+    with pytest.raises(abi.AbftError):
+        abi.abft_schedule(1, -1.0, 0xFFFFFFFF, (8, 8, 2), 0, 10)
+    with pytest.raises(abi.AbftError):
+        abi.abft_schedule(1, 0.5, 0xFFFFFFFF, (8, 8, 2), 5, 2)
+    assert len(abi.abft_schedule(1, 0.0, 0xFFFFFFFF, (8, 8, 2), 0, 10)) == 0
+
+
+def test_status_strings(abi):
+    assert abi.abft_status_string(0) == "ok"
+    assert "timed out" in abi.abft_status_string(5)

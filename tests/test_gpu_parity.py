@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded
+inputs.  Bar: identical sets of detected / located / corrected / recomputed points
+and rolled-back windows (outside the oracle's 5 % guard band), zero false positives,
+and grid values within 1e-5 relative error per 100 sweeps."""
+import numpy as np
+import pytest
+
+from paper_1909_00709_gb300 import inputs
+from _util import compare_events, gpu_context, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+ONLINE, OFFLINE, NONE = 1, 2, 0
+# a handful of shapes spanning several tiles and ragged tails in x and y
+SHAPES = [(64, 64, 8), (200, 37, 5), (129, 17, 3), (300, 130, 2), (33, 1, 4), (1, 7, 1), (257, 64, 9)]
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_00709_gb300 import abi, build
+    build.build()
+    abi.lib()
+    return abi
+
+
+def value_tol(steps):
+    return 1e-5 * max(1.0, steps / 100.0)
+
+
+@pytest.mark.parametrize("tile_y", [8, 16, 32])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_one_sweep_matches_eq1(abi, orc, shape, tile_y):
+    with gpu_context(abi, [shape], [3], tile_y=tile_y) as ctx:
+        ctx.step(1, NONE)
+        got = ctx.read(0)
+    ref = oracle_run(orc, shape, 3, 1, orc.MODE_NONE)["u"]
+    assert rel_err(got, ref) < 1e-6
+
+
+@pytest.mark.parametrize("acc", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5), (257, 64, 9)])
+def test_online_fault_free(abi, orc, shape, acc):
+    steps = 100
+    with gpu_context(abi, [shape], [5], acc=acc) as ctx:
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    assert len(ev) == 0, ev[:5]
+    ref = oracle_run(orc, shape, 5, steps, orc.MODE_ONLINE)
+    assert ref["n_events"] == 0
+    assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+def test_online_one_flip_every_10_steps_64x64x8(abi, orc):
+    """The small workload: 64x64x8, 100 sweeps, one seeded flip every 10 sweeps."""
+    shape, steps = (64, 64, 8), 100
+    flips = inputs.flips_periodic(shape, steps, 10, seed=0)
+    with gpu_context(abi, [shape], [0]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = oracle_run(orc, shape, 0, steps, orc.MODE_ONLINE, flips)
+    g, o = compare_events(ev, ref)
+    assert g == o
+    assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+@pytest.mark.parametrize("bit", list(range(32)))
+def test_online_each_bit(abi, orc, bit):
+    shape, steps = (64, 64, 8), 12
+    flips = inputs.flip_list([(5, 0, 3, 41, 17, bit)])
+    with gpu_context(abi, [shape], [1]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = oracle_run(orc, shape, 1, steps, orc.MODE_ONLINE, flips)
+    g, o = compare_events(ev, ref)
+    assert g == o
+    assert (len(o) == 1) == (bit >= 13)
+    assert rel_err(got, ref["u"]) < value_tol(steps) + (1e-3 if bit < 13 else 0)
+
+
+@pytest.mark.parametrize("case", ["two_by_two", "same_row", "same_col", "two_planes"])
+def test_online_multi_flip_patterns(abi, orc, case):
+    shape, steps = (200, 37, 5), 8
+    e = {"two_by_two": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 20, 150, 28)],
+         "same_row": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 5, 150, 28)],
+         "same_col": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 30, 7, 28)],
+         "two_planes": [(3, 0, 1, 5, 7, 30), (3, 0, 4, 30, 199, 27)]}[case]
+    flips = inputs.flip_list(e)
+    with gpu_context(abi, [shape], [2]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = oracle_run(orc, shape, 2, steps, orc.MODE_ONLINE, flips)
+    g, o = compare_events(ev, ref)
+    assert g == o and len(o) >= 2
+    assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5)])
+def test_offline_rollback_parity(abi, orc, shape):
+    steps = 40
+    flips = inputs.flip_list([(20, 0, 2, 10, 11, 28), (35, 0, 1, 3, 4, 30), (9, 0, 0, 1, 2, 3)])
+    with gpu_context(abi, [shape], [4]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(steps, OFFLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+        cnt = ctx.counters()
+    ref = oracle_run(orc, shape, 4, steps, orc.MODE_OFFLINE, flips, delta=16)
+    g, o = compare_events(ev, ref)
+    assert g == o
+    assert cnt["rollbacks"] == ref["n_rollbacks"] == 2
+    # rolled-back windows are recomputed without faults; the surviving low-bit flip stays
+    assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+def test_offline_fault_free_equals_unprotected(abi):
+    shape = (129, 17, 3)
+    with gpu_context(abi, [shape], [6]) as a, gpu_context(abi, [shape], [6]) as b:
+        a.step(37, OFFLINE)
+        b.step(37, NONE)
+        assert len(a.events()) == 0
+        np.testing.assert_array_equal(a.read(0), b.read(0))
+
+
+def test_two_grids_in_one_context(abi, orc):
+    shapes = [(64, 64, 8), (200, 37, 5)]
+    flips = inputs.flip_list([(4, 0, 3, 10, 20, 29), (6, 1, 2, 30, 100, 25)])
+    with gpu_context(abi, shapes, [7, 8]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(10, ONLINE)
+        ev = ctx.events()
+        for gi, (shape, seed) in enumerate(zip(shapes, [7, 8])):
+            fl = flips[flips["grid"] == gi]
+            ref = oracle_run(orc, shape, seed, 10, orc.MODE_ONLINE, fl)
+            g, o = compare_events(ev, ref, grid=gi)
+            assert g == o and len(o) == 1
+            assert rel_err(ctx.read(gi), ref["u"]) < 1e-5
+
+
+def test_seeded_schedule_run_matches_oracle(abi, orc):
+    shape, steps, seed, rate = (96, 80, 6), 60, 99, 0.3
+    with gpu_context(abi, [shape], [9]) as ctx:
+        ctx.inject(seed, rate, 0xFFFFFFFF)
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+        cnt = ctx.counters()
+    sched = orc.schedule(seed, rate, 0xFFFFFFFF, shape, 0, steps)
+    assert cnt["flips_scheduled"] == len(sched)
+    ref = oracle_run(orc, shape, 9, steps, orc.MODE_ONLINE, sched)
+    g, o = compare_events(ev, ref)
+    assert g == o
+    assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+def test_verify_and_correct_point(abi, orc):
+    """abft_verify at zero distance after a corrupted online step is not possible; use
+    an unprotected sweep with a flip, then verify (chained) and correct (rollback)."""
+    shape = (64, 64, 8)
+    flips = inputs.flip_list([(2, 0, 3, 4, 5, 29)])
+    with gpu_context(abi, [shape], [10]) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(3, NONE)
+        n = ctx.verify()
+        assert n >= 2
+        fixed = ctx.correct()
+        assert fixed == 3
+        assert ctx.verify() == 0
+        got = ctx.read(0)
+    ref = oracle_run(orc, shape, 10, 3, orc.MODE_NONE)
+    assert rel_err(got, ref["u"]) < 1e-6
+
+
+def test_full_size_512x512x8_sampled(abi, orc):
+    """512x512x8 in the launch configuration the benchmark times: 1000 online sweeps
+    with seeded flips (rate 1e-3 per sweep) and a fault-free run.  The oracle checks
+    every scheduled flip (located where it was injected iff its bit is above the
+    closed-form detection boundary) and one final sweep point by point."""
+    shape, steps = (512, 512, 8), 1000
+    ff_events = None
+    with gpu_context(abi, [shape], [1]) as ctx:
+        ctx.step(steps, ONLINE)
+        ff_events = ctx.events()
+        ff = ctx.read(0)
+    assert len(ff_events) == 0
+    seeds = [1, 2, 3]
+    located = 0
+    for s in seeds:
+        sched = orc.schedule(s, 1e-3, 0xFFFFFFFF, shape, 0, steps)
+        with gpu_context(abi, [shape], [1]) as ctx:
+            ctx.inject(s, 1e-3, 0xFFFFFFFF)
+            ctx.step(steps, ONLINE)
+            ev = ctx.events()
+            got = ctx.read(0)
+        expect = {(int(f["step"]), int(f["z"]), int(f["y"]), int(f["x"]), 1) for f in sched if f["bit"] >= 16}
+        got_set = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"])) for e in ev}
+        assert got_set == expect
+        located += len(expect)
+        low = [f for f in sched if f["bit"] < 16]
+        if not low:
+            assert rel_err(got, ff) < 1e-5
+    # one more sweep from the GPU's final state against Eq. (1) in FP64
+    co = inputs.hotspot_coeffs(*shape)
+    _, power = inputs.grid_inputs(*shape, seed=1)
+    st = orc.Stencil(shape, orc.hotspot_points(co))
+    ref = orc.sweep(st, orc.source_term(power, co), ff.astype(np.float64))
+    with abi.Context([shape], [ff], [power], [co]) as c2:  # the final state as a new start
+        c2.step(1, NONE)
+        one = c2.read(0)
+    assert rel_err(one, ref) < 1e-6
