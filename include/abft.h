@@ -197,6 +197,29 @@ ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, d
 ABFT_API const char* abft_last_error(const abft_ctx* ctx);
 ABFT_API const char* abft_status_string(abft_status s);
 
+/* One protected sweep (Eq. 1 with the fused checksum epilogue) and the per-plane
+   checksums a[z][x], b[z][y] of its result, for callers that cannot allocate
+   device memory: code living inside another framework's memory pool, plug-ins
+   whose host forbids device allocations once running, or code that must not
+   allocate while a stream is being captured.  The paper has no counterpart; this
+   is a packaging of the library's own sweep.
+   The caller owns every buffer: u_in, C (constant term) and u_out are device FP32
+   grids with rows of `pitch` elements (pitch >= nx, a multiple of 4; pointers
+   16-byte aligned; u_out != u_in); a_out (nz*nx) and b_out (nz*ny) are device FP64.
+   No context, workspace or allocation: the per-tile partial sums live in one fixed
+   8 MiB device array inside the library, held by every GPU that loads it until
+   the process exits.  Grids whose partials do not fit are refused.  The first call
+   on a device looks up that array's address (once per device, with the device
+   current): make it before any stream capture.  All calls share the array, so
+   calls that overlap on the GPU race; serialise them.  Work is enqueued on
+   `stream` (cudaStream_t) and the call returns without synchronising.
+   Errors: ABFT_E_INVAL (NULL or misaligned pointers, bad sizes, grid too large for
+   the array), ABFT_E_CUDA. */
+ABFT_API abft_status abft_sweep_checksums_static(const float* u_in, const float* C, float* u_out,
+                                                 double* a_out, double* b_out, int32_t nx, int32_t ny,
+                                                 int32_t nz, int64_t pitch, const abft_coeffs* coeffs,
+                                                 void* stream);
+
 /* Release host state and graphs; the workspace is the caller's to free. */
 ABFT_API void abft_destroy(abft_ctx* ctx);
 

@@ -25,7 +25,7 @@ STATUS = {0: "ABFT_OK", 1: "ABFT_E_INVAL", 2: "ABFT_E_CUDA", 3: "ABFT_E_NOMEM", 
 EXPORTS = ("abft_default_options", "abft_workspace_bytes", "abft_init", "abft_step", "abft_verify",
            "abft_correct", "abft_inject", "abft_inject_list", "abft_schedule", "abft_events",
            "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
-           "abft_last_error", "abft_status_string", "abft_destroy")
+           "abft_last_error", "abft_status_string", "abft_destroy", "abft_sweep_checksums_static")
 
 
 class abft_grid(ct.Structure):
@@ -146,6 +146,22 @@ def abft_schedule(seed: int, rate: float, bitmask: int, shape, t_begin: int, t_e
     if n < 0:
         raise AbftError(1, "abft_schedule: invalid arguments")
     return out[:min(n, cap)].copy()
+
+
+def abft_sweep_checksums_static(u_in: int, C: int, u_out: int, a_out: int, b_out: int, shape, pitch: int,
+                                co: dict, stream: int = 0) -> int:
+    """One protected sweep plus the checksums of its result, with no allocation
+    (device pointers in, device pointers out).  Returns the abft_status code."""
+    L = lib()
+    f = L.abft_sweep_checksums_static
+    if f.argtypes is None:
+        P = ct.c_void_p
+        f.argtypes = [P, P, P, P, P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int64,
+                      ct.POINTER(abft_coeffs), P]
+        f.restype = ct.c_int
+    nx, ny, nz = shape
+    c = _coeffs(co)
+    return f(u_in, C, u_out, a_out, b_out, nx, ny, nz, pitch, ct.byref(c), stream)
 
 
 def abft_status_string(s: int) -> str:
