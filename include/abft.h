@@ -92,6 +92,10 @@ typedef struct {
   int32_t graph_steps;      /* sweeps per captured CUDA graph; 0 disables graphs */
   int32_t tile_y;           /* rows per sweep tile (8, 16 or 32); 0 = library default */
   int32_t max_flips_per_step; /* schedule capacity per step and grid (<= 511) */
+  int32_t persistent;       /* 1: run online/unprotected sweeps in one persistent cooperative
+                               launch per grid and schedule chunk; 0: one launch per kernel */
+  int32_t shallow;          /* 1: grids with nz <= 16 use whole-column tiles (all planes staged
+                               at once); 0: always stream the planes */
   void* stream;             /* cudaStream_t used for all device work */
 } abft_options;
 
@@ -116,7 +120,8 @@ typedef struct {
 } abft_counters;
 
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
-   sweeps, default tile, 64 flips per step, NULL stream. */
+   sweeps, default tile, 64 flips per step, persistent launches, whole-column tiles for
+   shallow grids, NULL stream. */
 ABFT_API void abft_default_options(abft_options* opt);
 
 /* Bytes of device workspace abft_init needs for these grids and options
@@ -187,11 +192,12 @@ ABFT_API abft_status abft_current(abft_ctx* ctx, int32_t grid, float** dev_ptr, 
 
 ABFT_API abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out);
 
-/* Measurement hook: run n sweeps of `mode` without graphs, bracketing every kernel
-   launch with CUDA events on the context stream, and report per kernel kind the
-   summed milliseconds and launch counts (arrays of length ABFT_KERNEL_KINDS, in the
-   order sweep-plain, sweep-protected, check-online, check-offline, chain, other). */
-#define ABFT_KERNEL_KINDS 6
+/* Measurement hook: run n sweeps of `mode`, bracketing every kernel launch with CUDA
+   events on the context stream, and report per kernel kind the summed milliseconds
+   and launch counts (arrays of length ABFT_KERNEL_KINDS, in the order sweep-plain,
+   sweep-protected, check-online, check-offline, chain, other, persistent-plain,
+   persistent-protected). */
+#define ABFT_KERNEL_KINDS 8
 ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, double* ms, int64_t* launches);
 
 ABFT_API const char* abft_last_error(const abft_ctx* ctx);

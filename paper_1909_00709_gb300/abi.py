@@ -17,7 +17,8 @@ from . import build as _build
 MODE_NONE, MODE_ONLINE, MODE_OFFLINE = 0, 1, 2
 ACC_FP32, ACC_TWOSUM, ACC_FP64 = 0, 1, 2
 EV_CORRECTED, EV_RECOMPUTED, EV_ROLLBACK = 1, 2, 3
-KERNEL_KINDS = ("sweep_plain", "sweep_protected", "check_online", "check_offline", "chain", "other")
+KERNEL_KINDS = ("sweep_plain", "sweep_protected", "check_online", "check_offline", "chain", "other",
+                "persistent_plain", "persistent_protected")
 
 STATUS = {0: "ABFT_OK", 1: "ABFT_E_INVAL", 2: "ABFT_E_CUDA", 3: "ABFT_E_NOMEM", 4: "ABFT_E_STATE",
           5: "ABFT_E_TIMEOUT", 6: "ABFT_E_UNCORRECTABLE", 7: "ABFT_E_TRUNCATED"}
@@ -39,7 +40,8 @@ class abft_coeffs(ct.Structure):
 class abft_options(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
-                ("max_flips_per_step", ct.c_int32), ("stream", ct.c_void_p)]
+                ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
+                ("stream", ct.c_void_p)]
 
 
 class abft_counters(ct.Structure):
@@ -273,8 +275,9 @@ class Context:
         return {k: getattr(c, k) for k, _ in abft_counters._fields_}
 
     def time_kernels(self, n: int, mode: int) -> dict:
-        ms = (ct.c_double * 6)()
-        la = (ct.c_int64 * 6)()
+        nk = len(KERNEL_KINDS)
+        ms = (ct.c_double * nk)()
+        la = (ct.c_int64 * nk)()
         self._check(lib().abft_time_kernels(self.h, n, mode, ms, la), "abft_time_kernels", ok=(0, 7))
         return {k: (ms[i], la[i]) for i, k in enumerate(KERNEL_KINDS)}
 

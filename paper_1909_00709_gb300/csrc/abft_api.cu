@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -33,7 +34,7 @@ struct Bump {
 };
 
 struct GridPlan {
-  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, fcnt, fidx;
+  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx;
 };
 
 struct Plan {
@@ -42,7 +43,13 @@ struct Plan {
   int64_t sched_cap;
 };
 
-int pick_ty(const abft_options& o) { return o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32 ? o.tile_y : 16; }
+bool is_shallow(const abft_options& o, const abft_grid& G) { return o.shallow && G.nz <= kShallowMaxZ; }
+
+// rows per tile: streaming tiles default to 16, whole-column tiles to 8 (16 allowed)
+int pick_ty(const abft_options& o, const abft_grid& G) {
+  if (is_shallow(o, G)) return o.tile_y == 16 && G.nz <= 8 ? 16 : 8;
+  return o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32 ? o.tile_y : 16;
+}
 
 size_t partial_elem(int acc) { return acc == ABFT_ACC_FP32 ? 4 : 8; }
 
@@ -54,17 +61,18 @@ bool valid_grid(const abft_grid& g) {
 bool valid_options(const abft_options& o) {
   return o.eps > 0 && std::isfinite(o.eps) && o.delta >= 1 && o.acc >= 0 && o.acc <= 2 &&
          o.event_capacity >= 1 && o.graph_steps >= 0 && o.max_flips_per_step >= 0 &&
-         o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32);
+         o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
+         (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
   if (!grids || n < 1 || !valid_options(o)) return false;
   Bump b;
-  const int ty = pick_ty(o);
   P->g.resize(n);
   for (int i = 0; i < n; ++i) {
     const abft_grid& G = grids[i];
     if (!valid_grid(G)) return false;
+    const int ty = pick_ty(o, G);
     const size_t px = align_up(G.nx, 32);
     const size_t vol = px * G.ny * G.nz * sizeof(float);
     const size_t na = (size_t)G.nz * G.nx * 8, nb = (size_t)G.nz * G.ny * 8;
@@ -78,6 +86,8 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     for (int k = 0; k < 3; ++k) { p.AP[k] = b.take(na); p.BP[k] = b.take(nb); }
     p.PA = b.take(nty * G.nz * ntx * kTX * partial_elem(o.acc));
     p.PB = b.take(ntx * G.nz * (size_t)G.ny * partial_elem(o.acc));
+    p.PA2 = b.take(nty * G.nz * ntx * kTX * partial_elem(o.acc));
+    p.PB2 = b.take(ntx * G.nz * (size_t)G.ny * partial_elem(o.acc));
     p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
   }
@@ -161,8 +171,10 @@ cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUte
   cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.ny * 4};
   cuuint32_t ebox[3] = {1, 1, 1};
-  cuuint32_t ubox[3] = {(cuuint32_t)kUW, (cuuint32_t)(ty + 2), 1};
-  cuuint32_t cbox[3] = {(cuuint32_t)kTX, (cuuint32_t)ty, 1};
+  // streaming tiles stage one plane per box, whole-column tiles all nz planes
+  const cuuint32_t depth = g.shallow ? (cuuint32_t)g.nz : 1u;
+  cuuint32_t ubox[3] = {(cuuint32_t)kUW, (cuuint32_t)(ty + 2), depth};
+  cuuint32_t cbox[3] = {(cuuint32_t)kTX, (cuuint32_t)ty, depth};
   for (int k = 0; k < 4; ++k) {
     CUtensorMap* m = k < 3 ? &tm_u[k] : tm_c;
     void* base = k < 3 ? (void*)g.u[k] : (void*)g.C;
@@ -362,6 +374,49 @@ abft_status ensure_checksums(abft_ctx* ctx, int gi) {
   return ABFT_OK;
 }
 
+// `n` sweeps of every grid, one persistent cooperative launch per grid
+abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
+  const Launch L = launcher(ctx);
+  const bool prot = mode == ABFT_MODE_ONLINE;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    if (prot) {
+      abft_status s = ensure_checksums(ctx, gi);
+      if (s) return s;
+    }
+    const GridDev& g = ctx->g[gi];
+    const int c = ctx->cur[gi];
+    int p, q;
+    if (prot) {
+      p = (c + 1) % 3;
+      q = c;
+    } else if (c == ctx->ref[gi]) {
+      p = other_than(c, -1);
+      q = other_than(c, p);
+    } else {
+      p = other_than(c, ctx->ref[gi]);
+      q = c;
+    }
+    // zero the per-sweep fail counters and the barrier arrival count (contiguous)
+    static_assert(offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, fails) + 3 * sizeof(unsigned),
+                  "fails[] and bar[0] must be contiguous");
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned), ctx->stream));
+    int blocks = 0;
+    CK(run(ctx, prot ? kKPersistProt : kKPersistPlain, [&] {
+      return launch_persistent(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], ctx->step, (int)n, c, p, q, prot, &blocks);
+    }));
+    ctx->cur[gi] = prot ? (int)((c + n) % 3) : (((n - 1) & 1) ? q : p);
+    if (prot) {
+      ctx->ref[gi] = ctx->cur[gi];
+      ctx->ref_step[gi] = ctx->step + n;
+      ctx->ck_valid[gi] = 1;
+    } else {
+      ctx->ck_valid[gi] = 0;
+    }
+  }
+  ctx->step += n;
+  return ABFT_OK;
+}
+
 // one sweep of every grid; protected sweeps write partial checksums
 abft_status sweep_all(abft_ctx* ctx, int mode) {
   const Launch L = launcher(ctx);
@@ -544,6 +599,8 @@ void abft_default_options(abft_options* o) {
   o->graph_steps = 50;
   o->tile_y = 0;
   o->max_flips_per_step = 64;
+  o->persistent = 1;
+  o->shallow = 1;
   o->stream = nullptr;
 }
 
@@ -628,7 +685,6 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   ctx->grids.assign(grids, grids + n_grids);
   ctx->co.assign(coeffs, coeffs + n_grids);
   char* ws = (char*)workspace;
-  const int ty = pick_ty(*opt);
   ctx->g.resize(n_grids);
   ctx->ctrl = (DevCtrl*)(ws + P.ctrl);
   ctx->gctrl = (DevGridCtrl*)(ws + P.gctrl);
@@ -651,9 +707,10 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     memset(&g, 0, sizeof g);
     g.nx = G.nx; g.ny = G.ny; g.nz = G.nz;
     g.px = (int)align_up(G.nx, 32);
-    g.ty = ty;
+    g.ty = pick_ty(*opt, G);
+    g.shallow = is_shallow(*opt, G) ? 1 : 0;
     g.ntx = (G.nx + kTX - 1) / kTX;
-    g.nty = (G.ny + ty - 1) / ty;
+    g.nty = (G.ny + g.ty - 1) / g.ty;
     g.pa_stride = g.ntx * kTX;
     g.acc = opt->acc;
     g.gid = i;
@@ -672,6 +729,8 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.cy = (double*)(ws + p.cy);
     g.PA = ws + p.PA;
     g.PB = ws + p.PB;
+    g.PA2 = ws + p.PA2;
+    g.PB2 = ws + p.PB2;
     g.fcnt = (int*)(ws + p.fcnt);
     g.fidx = (int*)(ws + p.fidx);
     g.gc = ctx->gctrl + i;
@@ -703,7 +762,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.C, g.cx, g.cy); }));
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[0], g.A[0], g.B[0]); }));
     char e[256];
-    if (make_tensor_maps(g, ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess) {
+    if (make_tensor_maps(g, g.ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess) {
       st = fail(ctx, ABFT_E_CUDA, "%s", e);
       return bail(st);
     }
@@ -766,6 +825,11 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
     if (s) return s;
     if (mode == ABFT_MODE_OFFLINE) {
       s = offline_window(ctx, covered);
+      if (s) return s;
+      continue;
+    }
+    if (ctx->opt.persistent && covered > 0) {
+      s = persistent_all(ctx, covered, mode);
       if (s) return s;
       continue;
     }

@@ -16,6 +16,7 @@ constexpr int kUW = kTX + 2 * kHaloX;  // width of the staged u tile
 constexpr int kFCap = 64;         // failing entries kept per plane and vector
 constexpr int kLocalFlips = 32;   // flips a tile can apply in one sweep
 constexpr int kSchedSteps = 4096; // sweeps covered by one uploaded schedule chunk
+constexpr int kShallowMaxZ = 16;  // grids this shallow are swept with whole-column tiles
 constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side wait loop
 
 // sticky device status bits
@@ -28,7 +29,7 @@ enum : unsigned {
 
 // kernel kinds for launch accounting and abft_time_kernels
 enum KernelKind { kKSweepPlain = 0, kKSweepProt = 1, kKCheckOnline = 2, kKCheckOffline = 3,
-                  kKChain = 4, kKOther = 5 };
+                  kKChain = 4, kKOther = 5, kKPersistPlain = 6, kKPersistProt = 7 };
 
 struct Coef {
   float cc, cw, ce, cn, cs, cb, ct;
@@ -52,6 +53,9 @@ struct DevGridCtrl {
   unsigned int done_check;
   unsigned int done_aux;
   unsigned int pad;
+  unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
+  unsigned int bar[2];      // grid barrier of the persistent kernel: arrivals, generation
+  unsigned int pad2;
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
 };
@@ -62,6 +66,7 @@ struct GridDev {
   int ntx, nty, ty;         // sweep tiles along x and y, rows per tile
   int pa_stride;            // row stride of the a-partials (ntx * kTX)
   int acc;                  // abft_acc
+  int shallow;              // 1: whole-column tiles (all nz planes staged at once)
   int gid;
   Coef k;
   double eps;
@@ -71,6 +76,7 @@ struct GridDev {
   double* A[3]; double* B[3];  // checksums of the state held in u[i]
   double* AP[3]; double* BP[3];  // interpolated vectors (prediction, chain ping-pong, fresh sums)
   void* PA; void* PB;       // per-tile partial checksums of the last protected sweep
+  void* PA2; void* PB2;     // second set: the persistent kernel alternates by sweep parity
   int* fcnt;                // [nz][2] failing-entry counts (a, b)
   int* fidx;                // [nz][2][kFCap] failing indices
   DevGridCtrl* gc;
@@ -105,6 +111,8 @@ cudaError_t launch_chain(const Launch& L, const GridDev& g, const double* a_in, 
                          double* a_out, double* b_out);
 cudaError_t launch_compare(const Launch& L, const GridDev& g, const double* ap, const double* bp,
                            const double* a, const double* b);
+cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
+                              long long step0, int n_steps, int first_in, int p, int q, bool prot, int* blocks);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);
 

@@ -25,13 +25,13 @@ __device__ __forceinline__ float point_update(const GridDev& g, const float* __r
                                               int z, int y, int x) {
   const size_t plane = (size_t)g.ny * g.px;
   const float* p = u + (size_t)z * plane + (size_t)y * g.px + x;
-  const float c = p[0];
-  const float w = x > 0 ? p[-1] : c;
-  const float e = x < g.nx - 1 ? p[1] : c;
-  const float n = y > 0 ? p[-g.px] : c;
-  const float s = y < g.ny - 1 ? p[g.px] : c;
-  const float b = z > 0 ? p[-(ptrdiff_t)plane] : c;
-  const float t = z < g.nz - 1 ? p[plane] : c;
+  const float c = __ldcg(p);
+  const float w = x > 0 ? __ldcg(p - 1) : c;
+  const float e = x < g.nx - 1 ? __ldcg(p + 1) : c;
+  const float n = y > 0 ? __ldcg(p - g.px) : c;
+  const float s = y < g.ny - 1 ? __ldcg(p + g.px) : c;
+  const float b = z > 0 ? __ldcg(p - (ptrdiff_t)plane) : c;
+  const float t = z < g.nz - 1 ? __ldcg(p + plane) : c;
   const float C = g.C[(size_t)z * plane + (size_t)y * g.px + x];
   return hs_update(g.k, c, w, e, n, s, b, t, C);
 }
@@ -123,6 +123,56 @@ __device__ __forceinline__ void fence_barrier_init() {
 
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// order this thread's generic-proxy global writes before later async-proxy (TMA) reads
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch: count[0] arrivals, count[1] generation.
+// The wait is bounded; on timeout the status word records it and every later
+// barrier returns at once, so a broken launch ends instead of hanging.  Returns
+// false once the launch is poisoned.  All threads of every block must call it.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, DevCtrl* ctrl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = (ld_acquire_u32(&ctrl->status) & kStTimeout) == 0;
+    if (ok) {
+      const unsigned gen = ld_acquire_u32(&count[1]);
+      __threadfence();
+      const unsigned arrived = atomicAdd(&count[0], 1u) + 1u;
+      if (arrived == gridDim.x * gridDim.y * gridDim.z) {
+        atomicExch(&count[0], 0u);
+        __threadfence();
+        st_release_u32(&count[1], gen + 1u);
+      } else {
+        unsigned spins = 0;
+        while (ld_acquire_u32(&count[1]) == gen) {
+          if (++spins > kSpinLimit || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
+            set_status(ctrl, kStTimeout);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {

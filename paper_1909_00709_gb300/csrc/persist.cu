@@ -1,0 +1,282 @@
+// Persistent cooperative kernels: many sweeps of one grid in one launch.
+//
+// Every CTA stays resident for the whole run and owns a fixed set of 128 x TY tiles;
+// sweeps are separated by a grid barrier instead of a kernel boundary.
+//
+// Unprotected (k_persist_plain): sweep, barrier, repeat.
+//
+// Online (k_persist_online), with the check one sweep behind the sweep:
+//   iteration k (sweep index s = step0 + k), buffers rotate u^{s-1}, u^s, u^{s+1}:
+//     a. start the TMA loads of the first tile of sweep s;
+//     b. check u^s: every thread takes a slice of the checksum entries (cross-tile
+//        reduction of the partials sweep s-1 wrote, Theorem 1 from a^{s-1}, b^{s-1},
+//        the Sec. 3.4 test), overlapping the load latency;
+//     c. sweep u^s -> u^{s+1} (partials into the other partial buffer);
+//     d. grid barrier;
+//     e. only if some entry of u^s failed: block 0 locates and corrects u^s
+//        (Sec. 3.5, lines recomputed from u^{s-1}) and then repairs u^{s+1}: every
+//        point whose stencil read a repaired point is recomputed from the repaired
+//        u^s (with the same arithmetic as the sweep, flips of sweep s+1 re-applied)
+//        and the partials of the touched tile rows and columns are recomputed with
+//        the sweep epilogue's exact arithmetic; a second barrier publishes it.
+//   A final check of the last output ends the launch.  The result (grid, events,
+//   checksums) is bit-identical to checking after every sweep, with one barrier
+//   per sweep in the fault-free case instead of three.
+// Barrier waits are bounded: on timeout the status word is set and the launch winds
+// down instead of hanging.
+#include "check_dev.cuh"
+#include "sweep_tile.cuh"
+
+namespace abft {
+
+struct PersistArgs {
+  CUtensorMap tm_u[3];
+  CUtensorMap tm_c;
+  GridDev g;
+  long long step0;   // sweep index of the first sweep of this launch
+  int n_steps;
+  int first_in;      // buffer of the first sweep's input
+  int p, q;          // then outputs alternate p, q, p, ... (sweep k >= 1 reads the previous output)
+};
+
+template <class Tiles>
+__global__ void __launch_bounds__(256, 2)
+    k_persist_plain(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev,
+                    const DevSched sched) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const GridDev& g = a.g;
+  Tiles tiles;
+  tiles.setup(smem_raw, g.nz);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) prefetch_tensormap(&a.tm_u[k]);
+    prefetch_tensormap(&a.tm_c);
+  }
+  __syncthreads();
+  const int ntiles = g.ntx * g.nty;
+  const bool resident_c = (int)gridDim.x >= ntiles;  // one tile per CTA: C stays in shared memory
+  bool ok = true;
+  for (int k = 0; k < a.n_steps && ok; ++k) {
+    const int in = k == 0 ? a.first_in : ((k & 1) ? a.p : a.q);
+    const int out = (k & 1) ? a.q : a.p;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      tiles.issue(&a.tm_u[in], &a.tm_c, g, tile % g.ntx, tile / g.ntx, a.step0 + k, ctrl, sched,
+                  !resident_c || k == 0);
+      tiles.template run<false, ABFT_ACC_FP32>(&a.tm_u[in], &a.tm_c, g, g.u[out], tile % g.ntx, tile / g.ntx, ctrl,
+                                               0);
+    }
+    ok = grid_barrier(g.gc->bar, ctrl);
+  }
+  if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
+}
+
+// flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
+__device__ __forceinline__ float reapply_flips(float v, const GridDev& g, DevCtrl* ctrl, const DevSched& sched,
+                                               long long step, int z, int y, int x) {
+  if (!ctrl->inject_enabled) return v;
+  const long long i = step - ctrl->sched_t0;
+  if (i < 0 || i >= ctrl->sched_n) return v;
+  for (int k = sched.off[i]; k < sched.off[i + 1]; ++k) {
+    const DevFlip f = sched.flips[k];
+    if (f.grid == g.gid && f.target == 0 && f.z == z && f.y == y && f.x == x)
+      v = __int_as_float(__float_as_int(v) ^ (1 << (f.bit & 31)));
+  }
+  return v;
+}
+
+// Box (z, y, x ranges) of u^{s+1} points whose stencil read something that the fix
+// f = (kind, z, y, x) of u^s changed.
+__device__ __forceinline__ void fix_box(const GridDev& g, int4 f, int lo[3], int hi[3]) {
+  const int zz = f.y, yy = f.z, xx = f.w;
+  lo[0] = max(zz - 1, 0); hi[0] = min(zz + 1, g.nz - 1);
+  if (f.x == kFixPlane || f.x == kFixCol) { lo[1] = 0; hi[1] = g.ny - 1; }
+  else { lo[1] = max(yy - 1, 0); hi[1] = min(yy + 1, g.ny - 1); }
+  if (f.x == kFixPlane || f.x == kFixRow) { lo[2] = 0; hi[2] = g.nx - 1; }
+  else { lo[2] = max(xx - 1, 0); hi[2] = min(xx + 1, g.nx - 1); }
+}
+
+// Block 0: after the fixes `sm.fix` of u^s, recompute the affected points of u^{s+1}
+// (the output of sweep `sweep_s`, whose flips are re-applied) and the partials
+// (buffer PA/PB) of every tile row and column that holds one.
+template <class Tiles, int TY, int ACC>
+__device__ void repair_next(const GridDev& g, const float* u_s, float* u_n, void* PA, void* PB, const ResolveSmem& sm,
+                            long long sweep_s, DevCtrl* ctrl, const DevSched& sched) {
+  const int nfix = sm.nfix;
+  const bool overflow = nfix > kFixCap;
+  const int nitems = overflow ? g.nz : nfix;
+  auto item = [&](int i) -> int4 {  // on overflow: every plane
+    return overflow ? make_int4(kFixPlane, i, -1, -1) : sm.fix[i];
+  };
+  for (int i = 0; i < nitems; ++i) {
+    int lo[3], hi[3];
+    fix_box(g, item(i), lo, hi);
+    const int ny = hi[1] - lo[1] + 1, nx = hi[2] - lo[2] + 1;
+    const long long vol = (long long)(hi[0] - lo[0] + 1) * ny * nx;
+    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
+      const int z = lo[0] + (int)(t / ((long long)ny * nx));
+      const int r = (int)(t % ((long long)ny * nx));
+      const int y = lo[1] + r / nx, x = lo[2] + r % nx;
+      const float v = reapply_flips(point_update(g, u_s, z, y, x), g, ctrl, sched, sweep_s, z, y, x);
+      u_n[((size_t)z * g.ny + y) * g.px + x] = v;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int i = 0; i < nitems; ++i) {
+    int lo[3], hi[3];
+    fix_box(g, item(i), lo, hi);
+    const int tx0 = lo[2] / kTX, tx1 = hi[2] / kTX;
+    const int ty0 = lo[1] / TY, ty1 = hi[1] / TY;
+    // row partials: one warp per (z, y, tile-x)
+    const int nrows = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (tx1 - tx0 + 1);
+    for (int t = warp; t < nrows; t += nwarps) {
+      const int ntx = tx1 - tx0 + 1, nyy = hi[1] - lo[1] + 1;
+      const int z = lo[0] + t / (nyy * ntx);
+      const int r = t % (nyy * ntx);
+      recompute_pb<ACC>(g, u_n, PB, tx0 + r % ntx, z, lo[1] + r / ntx);
+    }
+    // column partials: one thread per (z, x, tile-y)
+    const int xa = lo[2], xb = hi[2];
+    const int ncols = (hi[0] - lo[0] + 1) * (xb - xa + 1) * (ty1 - ty0 + 1);
+    for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
+      const int nxx = xb - xa + 1, nty = ty1 - ty0 + 1;
+      const int z = lo[0] + t / (nxx * nty);
+      const int r = t % (nxx * nty);
+      Tiles::template recompute_col<ACC>(g, u_n, PA, ty0 + r / nxx, z, xa + r % nxx);
+    }
+  }
+  __threadfence();
+  fence_proxy_async_global();  // u^{s+1} is read by TMA in the next sweep
+  __syncthreads();
+}
+
+template <class Tiles, int TY, int ACC>
+__global__ void __launch_bounds__(256, 2)
+    k_persist_online(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev,
+                     const DevSched sched) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ ResolveSmem rs;
+  const GridDev& g = a.g;
+  Tiles tiles;
+  tiles.setup(smem_raw, g.nz);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) prefetch_tensormap(&a.tm_u[k]);
+    prefetch_tensormap(&a.tm_c);
+  }
+  __syncthreads();
+  unsigned* bar = g.gc->bar;
+  const int ntiles = g.ntx * g.nty;
+  const int n_entries = g.nz * (g.nx + g.ny);
+  const int first_tile = blockIdx.x;
+  const bool resident_c = (int)gridDim.x >= ntiles;
+  bool ok = true;
+  for (int k = 0; k <= a.n_steps && ok; ++k) {
+    const long long s = a.step0 + k;
+    const int cur = (a.first_in + k) % 3, nxt = (a.first_in + k + 1) % 3, prv = (a.first_in + k + 2) % 3;
+    const int pb_cur = (int)(s & 1), pb_nxt = (int)((s + 1) & 1);
+    const bool sweep = k < a.n_steps, check = k > 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[(s + 1) % 3] = 0;  // last read two sweeps ago
+    // a. loads of the first tile of this sweep
+    if (sweep && first_tile < ntiles)
+      tiles.issue(&a.tm_u[cur], &a.tm_c, g, first_tile % g.ntx, first_tile / g.ntx, s, ctrl, sched,
+                  !resident_c || k == 0);
+    // b. check u^s against the interpolation from a^{s-1}, b^{s-1}
+    unsigned* any = &g.gc->fails[s % 3];
+    if (check)
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_entries; i += gridDim.x * blockDim.x)
+        check_entry<ACC>(g, prv, cur, i, any, pb_cur);
+    // c. sweep u^s -> u^{s+1}
+    if (sweep) {
+      for (int tile = first_tile; tile < ntiles; tile += gridDim.x) {
+        if (tile != first_tile)
+          tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, true);
+        tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl, pb_nxt);
+      }
+    }
+    // d.
+    ok = grid_barrier(bar, ctrl);
+    if (!ok || !check) continue;
+    // e. rare: locate, correct, repair the speculative sweep
+    if (ld_acquire_u32(any) != 0) {
+      if (blockIdx.x == 0) {
+        // u^s is the output of sweep s - 1; u^{s+1} that of sweep s
+        resolve_planes_into(rs, g, g.u[prv], g.u[cur], g.A[cur], g.B[cur], g.AP[0], g.BP[0], s - 1, ctrl, ev,
+                            &g.gc->unresolved);
+        __syncthreads();
+        if (sweep)
+          repair_next<Tiles, TY, ACC>(g, g.u[cur], g.u[nxt], pb_nxt ? g.PA2 : g.PA, pb_nxt ? g.PB2 : g.PB, rs, s,
+                                      ctrl, sched);
+        fence_proxy_async_global();
+      }
+      ok = grid_barrier(bar, ctrl);
+    }
+  }
+  if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
+}
+
+template <class Tiles, int TY, bool PROT, int ACC>
+static cudaError_t launch_persist_t(const Launch& L, const PersistArgs& a, int* blocks_out) {
+  auto kern = PROT ? k_persist_online<Tiles, TY, ACC> : k_persist_plain<Tiles>;
+  const int smem = Tiles::smem_bytes(a.g.nz);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int ntiles = a.g.ntx * a.g.nty;
+  int blocks = per_sm * sms;
+  if (blocks > ntiles) blocks = ntiles;
+  if (blocks < 1) return cudaErrorInvalidConfiguration;
+  // every CTA should own the same number of tiles: trim to the largest grid that does
+  const int rounds = (ntiles + blocks - 1) / blocks;
+  blocks = (ntiles + rounds - 1) / rounds;
+  *blocks_out = blocks;
+  DevCtrl* ctrl = L.ctrl;
+  abft_event* ev = L.events;
+  DevSched sched = L.sched;
+  void* args[] = {(void*)&a, (void*)&ctrl, (void*)&ev, (void*)&sched};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, smem, L.s);
+}
+
+template <class Tiles, int TY>
+static cudaError_t launch_persist_ty(const Launch& L, const PersistArgs& a, bool prot, int* blocks) {
+  if (!prot) return launch_persist_t<Tiles, TY, false, ABFT_ACC_FP32>(L, a, blocks);
+  switch (a.g.acc) {
+    case ABFT_ACC_TWOSUM: return launch_persist_t<Tiles, TY, true, ABFT_ACC_TWOSUM>(L, a, blocks);
+    case ABFT_ACC_FP64: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP64>(L, a, blocks);
+    default: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP32>(L, a, blocks);
+  }
+}
+
+cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
+                              long long step0, int n_steps, int first_in, int p, int q, bool prot, int* blocks) {
+  PersistArgs a;
+  for (int k = 0; k < 3; ++k) a.tm_u[k] = tm_u[k];
+  a.tm_c = tm_c;
+  a.g = g;
+  a.step0 = step0;
+  a.n_steps = n_steps;
+  a.first_in = first_in;
+  a.p = p;
+  a.q = q;
+  if (g.shallow) {
+    switch (g.ty) {
+      case 8: return launch_persist_ty<ShallowTiles<8>, 8>(L, a, prot, blocks);
+      case 16: return launch_persist_ty<ShallowTiles<16>, 16>(L, a, prot, blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (g.ty) {
+    case 8: return launch_persist_ty<StreamTiles<8>, 8>(L, a, prot, blocks);
+    case 16: return launch_persist_ty<StreamTiles<16>, 16>(L, a, prot, blocks);
+    case 32: return launch_persist_ty<StreamTiles<32>, 32>(L, a, prot, blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace abft

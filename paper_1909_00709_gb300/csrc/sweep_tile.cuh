@@ -1,0 +1,652 @@
+// One tile of the stencil sweep of Eq. (1) with the per-plane checksums of Eq. (2)/(3)
+// fused into its epilogue (Sec. 3.2) and the flip-injection hook of Sec. 5.1.
+//
+// A CTA owns a 128 x TY column of the grid and streams it along z.  Plane tiles
+// (with a one-cell y halo and a 4-cell, 16-byte aligned x halo) and the matching
+// tiles of the constant term C are staged into a ring of S shared-memory stages by
+// TMA, one mbarrier per stage.  Every thread computes one float4 of each of its
+// rows; all seven neighbours come from shared memory, the x neighbours across
+// float4 boundaries by warp shuffles.  Clamped boundaries (Fig. 2) are selects on
+// the grid edges, since TMA fills out-of-range cells with zeros.
+//
+// The checksum epilogue sums exactly the stored values (after injection):
+//   b[z][y] partial: the row's 128 values, warp-shuffle reduction;
+//   a[z][x] partial: the tile's TY values per column, in registers per warp, then
+//                    one pass over shared memory by 128 threads (one per column).
+// Partials are written per tile and reduced across tiles in a fixed order by the
+// check, so results are bitwise repeatable.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace abft {
+
+template <int TY>
+struct SweepCfg {
+  static constexpr int NW = 8;                        // warps per CTA
+  static constexpr int S = TY <= 8 ? 6 : (TY <= 16 ? 5 : 4);  // ring depth (>= 4)
+  static constexpr int RPW = TY / NW;                 // rows per warp
+  static constexpr int UBOX = (TY + 2) * kUW * 4;     // bytes of a staged u box
+  static constexpr int UBOX_AL = (UBOX + 127) / 128 * 128;
+  static constexpr int CBOX = TY * kTX * 4;
+  static constexpr int STAGE = UBOX_AL + CBOX;        // multiple of 128
+  static constexpr int RED_HALF = NW * kTX * 8;       // one z-parity of the column reduction buffer
+  static constexpr int RED = 2 * RED_HALF;
+  static constexpr int FLIPS = kLocalFlips * 16 + 16;
+  static constexpr int SMEM = 128 + 128 + S * STAGE + RED + FLIPS;  // + slack to align the base
+  static_assert(TY % NW == 0, "TY must be a multiple of the warp count");
+  static_assert(S >= 4, "the ring must hold z-1, z, z+1 and one load in flight");
+};
+
+// ------------------------------------------------------------ accumulators
+// Per-thread column partials over this thread's rows (4 columns), their exchange
+// through shared memory (layout [warp][column]) and the row partial of one row.
+
+template <int ACC>
+struct AccA;
+
+template <>
+struct AccA<ABFT_ACC_FP32> {
+  float v[4];
+  __device__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.f; }
+  __device__ void add(const float (&m)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] += m[i];
+  }
+  __device__ void put(unsigned char* red, int warp, int lane) const {
+    reinterpret_cast<float4*>(red)[warp * 32 + lane] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  __device__ void store4(void* PA, size_t idx) const {  // this lane's 4 columns, directly
+    *reinterpret_cast<float4*>(static_cast<float*>(PA) + idx) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  // column c summed over the NW warp partials, written as partial PA[idx]
+  template <int NW>
+  __device__ static void column_store(const unsigned char* red, int c, void* PA, size_t idx) {
+    const float* r = reinterpret_cast<const float*>(red);
+    float s = r[c];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s += r[w * kTX + c];
+    static_cast<float*>(PA)[idx] = s;
+  }
+  __device__ static void row_store(const float (&m)[4], void* PB, size_t idx, bool write) {
+    float r = ((m[0] + m[1]) + m[2]) + m[3];
+    r = warp_sum(r);
+    if (write) static_cast<float*>(PB)[idx] = r;
+  }
+};
+
+template <>
+struct AccA<ABFT_ACC_TWOSUM> {
+  float h[4], l[4];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = l[i] = 0.f;
+  }
+  __device__ void add(const float (&m)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc2(h[i], l[i], m[i]);
+  }
+  __device__ void put(unsigned char* red, int warp, int lane) const {
+    float4* p = reinterpret_cast<float4*>(red);
+    p[warp * 32 + lane] = make_float4(h[0], h[1], h[2], h[3]);
+    p[8 * 32 + warp * 32 + lane] = make_float4(l[0], l[1], l[2], l[3]);  // lo half after 8 warps
+  }
+  __device__ void store4(void* PA, size_t idx) const {
+    float4* p = reinterpret_cast<float4*>(static_cast<float2*>(PA) + idx);
+    p[0] = make_float4(h[0], l[0], h[1], l[1]);
+    p[1] = make_float4(h[2], l[2], h[3], l[3]);
+  }
+  template <int NW>
+  __device__ static void column_store(const unsigned char* red, int c, void* PA, size_t idx) {
+    const float* r = reinterpret_cast<const float*>(red);
+    float hi = r[c], lo = r[8 * kTX + c];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+      acc2(hi, lo, r[w * kTX + c]);
+      lo += r[8 * kTX + w * kTX + c];
+    }
+    static_cast<float2*>(PA)[idx] = make_float2(hi, lo);
+  }
+  __device__ static void row_store(const float (&m)[4], void* PB, size_t idx, bool write) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc2(hi, lo, m[i]);
+    warp_sum2(hi, lo);
+    if (write) static_cast<float2*>(PB)[idx] = make_float2(hi, lo);
+  }
+};
+
+template <>
+struct AccA<ABFT_ACC_FP64> {
+  double v[4];
+  __device__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
+  __device__ void add(const float (&m)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] += (double)m[i];
+  }
+  __device__ void put(unsigned char* red, int warp, int lane) const {
+    double2* p = reinterpret_cast<double2*>(red) + (warp * 32 + lane) * 2;
+    p[0] = make_double2(v[0], v[1]);
+    p[1] = make_double2(v[2], v[3]);
+  }
+  __device__ void store4(void* PA, size_t idx) const {
+    double2* p = reinterpret_cast<double2*>(static_cast<double*>(PA) + idx);
+    p[0] = make_double2(v[0], v[1]);
+    p[1] = make_double2(v[2], v[3]);
+  }
+  template <int NW>
+  __device__ static void column_store(const unsigned char* red, int c, void* PA, size_t idx) {
+    const double* r = reinterpret_cast<const double*>(red);
+    double s = r[c];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s += r[w * kTX + c];
+    static_cast<double*>(PA)[idx] = s;
+  }
+  __device__ static void row_store(const float (&m)[4], void* PB, size_t idx, bool write) {
+    double r = (((double)m[0] + (double)m[1]) + (double)m[2]) + (double)m[3];
+    r = warp_sum(r);
+    if (write) static_cast<double*>(PB)[idx] = r;
+  }
+};
+
+// shared-memory layout of the sweep
+template <int TY>
+struct SweepSmem {
+  uint64_t* bar;
+  unsigned char* stages;
+  unsigned char* red;
+  int4* lflips;
+  int* nlf;
+  __device__ static SweepSmem carve(unsigned char* raw) {
+    using Cfg = SweepCfg<TY>;
+    SweepSmem m;
+    unsigned char* s = raw + ((128 - (smem_u32(raw) & 127)) & 127);  // TMA needs 128-byte alignment
+    m.bar = reinterpret_cast<uint64_t*>(s);
+    m.stages = s + 128;
+    m.red = m.stages + Cfg::S * Cfg::STAGE;
+    m.lflips = reinterpret_cast<int4*>(m.red + Cfg::RED);
+    m.nlf = reinterpret_cast<int*>(m.lflips + kLocalFlips);
+    return m;
+  }
+  __device__ float* stage_u(int s) const { return reinterpret_cast<float*>(stages + s * SweepCfg<TY>::STAGE); }
+  __device__ float* stage_c(int s) const {
+    return reinterpret_cast<float*>(stages + s * SweepCfg<TY>::STAGE + SweepCfg<TY>::UBOX_AL);
+  }
+  // thread 0 only, once per CTA
+  __device__ void init_barriers() const {
+    for (int s = 0; s < SweepCfg<TY>::S; ++s) mbar_init(&bar[s], 1);
+    fence_barrier_init();
+  }
+};
+
+// One tile (txi, tyi) of one sweep, u_in -> uout, in two halves: sweep_tile_issue()
+// starts the TMA loads and gathers the tile's flips, sweep_tile_run() streams the
+// planes.  Work that does not touch the ring (the persistent kernel's check) may run
+// between the two.  `seq` counts the plane loads this CTA has issued so far
+// (identical in every thread); the k-th load uses stage k % S with mbarrier phase
+// parity (k / S) & 1.  `pbuf` selects the partial-checksum buffers (PA/PB or
+// PA2/PB2).  Every thread must call both halves; the ring is idle before and after.
+template <int TY>
+__device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
+                                                 int txi, int tyi, long long step, DevCtrl* __restrict__ ctrl,
+                                                 const DevSched& sched, const SweepSmem<TY>& sm, unsigned seq) {
+  using Cfg = SweepCfg<TY>;
+  constexpr int S = Cfg::S;
+  const int tid = threadIdx.x;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+  const int nz = g.nz;
+  if (tid == 0) {
+    fence_proxy_async_global();  // grid data written by the generic proxy before TMA reads it
+    const int np = nz < S ? nz : S;
+    for (int p = 0; p < np; ++p) {
+      const int s = (int)((seq + p) % S);
+      mbar_expect_tx(&sm.bar[s], Cfg::UBOX + Cfg::CBOX);
+      tma_load_3d(sm.stage_u(s), tm_u, x0 - kHaloX, y0 - 1, p, &sm.bar[s]);
+      tma_load_3d(sm.stage_c(s), tm_c, x0, y0, p, &sm.bar[s]);
+    }
+    *sm.nlf = 0;
+  }
+  __syncthreads();
+  // flips of this sweep that land in this tile (Sec. 5.1: after the update, before the store)
+  if (ctrl->inject_enabled) {
+    const long long i = step - ctrl->sched_t0;
+    if (i >= 0 && i < ctrl->sched_n) {
+      const int b = sched.off[i], e = sched.off[i + 1];
+      for (int k = b + tid; k < e; k += blockDim.x) {
+        const DevFlip f = sched.flips[k];
+        if (f.grid == g.gid && f.target == 0 && f.x >= x0 && f.x < x0 + kTX && f.x < g.nx && f.y >= y0 &&
+            f.y < y0 + TY && f.y < g.ny && f.z >= 0 && f.z < nz && f.x >= 0 && f.y >= 0) {
+          const int j = atomicAdd(sm.nlf, 1);
+          if (j < kLocalFlips) sm.lflips[j] = make_int4(f.x, f.y, f.z, f.bit & 31);
+          else set_status(ctrl, kStFlipOverflow);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int TY, bool PROT, int ACC>
+__device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
+                                               float* __restrict__ uout, int txi, int tyi,
+                                               DevCtrl* __restrict__ ctrl, const SweepSmem<TY>& sm, unsigned& seq,
+                                               int pbuf) {
+  using Cfg = SweepCfg<TY>;
+  constexpr int S = Cfg::S, NW = Cfg::NW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+  const int nz = g.nz;
+  const unsigned base = seq;
+  void* PA = pbuf ? g.PA2 : g.PA;
+  void* PB = pbuf ? g.PB2 : g.PB;
+  auto issue = [&](int p) {  // TMA loads of plane p of this tile (thread 0 only)
+    const int s = (int)((base + p) % S);
+    mbar_expect_tx(&sm.bar[s], Cfg::UBOX + Cfg::CBOX);
+    tma_load_3d(sm.stage_u(s), tm_u, x0 - kHaloX, y0 - 1, p, &sm.bar[s]);
+    tma_load_3d(sm.stage_c(s), tm_c, x0, y0, p, &sm.bar[s]);
+  };
+  auto wait = [&](int p) {
+    const unsigned k = base + (unsigned)p;
+    mbar_wait(&sm.bar[k % S], (k / S) & 1u, ctrl);
+  };
+  const int nflip = min(*sm.nlf, kLocalFlips);
+  const int gx0 = x0 + 4 * lane;
+  const int last = g.nx - 1 - gx0;  // element holding x = nx-1, if 0..3
+
+  for (int z = 0; z < nz; ++z) {
+    if (z == 0) wait(0);
+    if (z + 1 < nz) wait(z + 1);
+    const float* Uc = sm.stage_u((int)((base + z) % S));
+    const float* Ub = z > 0 ? sm.stage_u((int)((base + z - 1) % S)) : Uc;
+    const float* Ut = z + 1 < nz ? sm.stage_u((int)((base + z + 1) % S)) : Uc;
+    const float* Cs = sm.stage_c((int)((base + z) % S));
+    AccA<ACC> acc;
+    if (PROT) acc.zero();
+#pragma unroll
+    for (int rr = 0; rr < Cfg::RPW; ++rr) {
+      const int r = warp + rr * NW;
+      const int y = y0 + r;
+      const int o = (r + 1) * kUW + kHaloX + 4 * lane;
+      const float4 c = *reinterpret_cast<const float4*>(Uc + o);
+      float4 n = *reinterpret_cast<const float4*>(Uc + o - kUW);
+      float4 s = *reinterpret_cast<const float4*>(Uc + o + kUW);
+      const float4 b = *reinterpret_cast<const float4*>(Ub + o);
+      const float4 t = *reinterpret_cast<const float4*>(Ut + o);
+      const float4 cs = *reinterpret_cast<const float4*>(Cs + r * kTX + 4 * lane);
+      float wl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float er = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (lane == 0) wl = Uc[o - 1];
+      if (lane == 31) er = Uc[o + 4];
+      if (y == 0) n = c;
+      if (y == g.ny - 1) s = c;
+      const float w0 = gx0 == 0 ? c.x : wl;
+      float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
+      if (last == 0) e0 = c.x;
+      if (last == 1) e1 = c.y;
+      if (last == 2) e2 = c.z;
+      if (last == 3) e3 = c.w;
+      float v[4];
+      v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
+      v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
+      v[2] = hs_update(g.k, c.z, c.y, e2, n.z, s.z, b.z, t.z, cs.z);
+      v[3] = hs_update(g.k, c.w, c.z, e3, n.w, s.w, b.w, t.w, cs.w);
+      if (nflip > 0) {
+        for (int f = 0; f < nflip; ++f) {
+          const int4 q = sm.lflips[f];
+          if (q.z == z && q.y == y) {
+            const int d = q.x - gx0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (d == i) v[i] = __int_as_float(__float_as_int(v[i]) ^ (1 << q.w));
+          }
+        }
+      }
+      const bool yv = y < g.ny;
+      float* dst = uout + ((size_t)z * g.ny + y) * g.px + gx0;
+      if (yv) {
+        if (last >= 3) {
+          *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (i <= last) dst[i] = v[i];
+        }
+      }
+      if (PROT) {
+        float m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
+        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.ny + y, yv && lane == 0);
+        acc.add(m);
+      }
+    }
+    if (PROT) acc.put(sm.red + (z & 1) * Cfg::RED_HALF, warp, lane);
+    __syncthreads();
+    if (tid == 0 && z >= 1 && z - 1 + S < nz) {
+      fence_proxy_async();
+      issue(z - 1 + S);
+    }
+    if (PROT && tid < kTX)
+      AccA<ACC>::template column_store<NW>(sm.red + (z & 1) * Cfg::RED_HALF, tid, PA,
+                                           ((size_t)tyi * nz + z) * g.pa_stride + x0 + tid);
+  }
+  seq = base + (unsigned)nz;
+  fence_proxy_async_global();  // this thread's grid stores, before any later TMA read of them
+  __syncthreads();             // the ring and the reduction buffer are idle again
+}
+
+template <int TY, bool PROT, int ACC>
+__device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
+                                           float* __restrict__ uout, int txi, int tyi, long long step,
+                                           DevCtrl* __restrict__ ctrl, const DevSched& sched,
+                                           const SweepSmem<TY>& sm, unsigned& seq, int pbuf = 0) {
+  sweep_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, seq);
+  sweep_tile_run<TY, PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, sm, seq, pbuf);
+}
+
+// ------------------------------------------------- partials, recomputed exactly
+// The same arithmetic, in the same order, as the sweep epilogue above, for one
+// column (a-partial) or one row (b-partial, one full warp) of one tile.  Used when
+// a repaired grid must yield the partials the sweep would have produced.
+
+template <int TY, int ACC>
+__device__ void recompute_pa(const GridDev& g, const float* __restrict__ u, void* PA, int tyi, int z, int x) {
+  constexpr int NW = SweepCfg<TY>::NW, RPW = SweepCfg<TY>::RPW;
+  const int y0 = tyi * TY;
+  auto val = [&](int r) -> float {
+    const int y = y0 + r;
+    return (y < g.ny && x < g.nx) ? __ldcg(u + ((size_t)z * g.ny + y) * g.px + x) : 0.f;
+  };
+  const size_t idx = ((size_t)tyi * g.nz + z) * g.pa_stride + x;
+  if (ACC == ABFT_ACC_FP32) {
+    float s = 0.f;
+    for (int w = 0; w < NW; ++w) {
+      float a = 0.f;
+      for (int rr = 0; rr < RPW; ++rr) a += val(w + rr * NW);
+      s = w == 0 ? a : s + a;
+    }
+    static_cast<float*>(PA)[idx] = s;
+  } else if (ACC == ABFT_ACC_TWOSUM) {
+    float hi = 0.f, lo = 0.f;
+    for (int w = 0; w < NW; ++w) {
+      float h = 0.f, l = 0.f;
+      for (int rr = 0; rr < RPW; ++rr) acc2(h, l, val(w + rr * NW));
+      if (w == 0) {
+        hi = h;
+        lo = l;
+      } else {
+        acc2(hi, lo, h);
+        lo += l;
+      }
+    }
+    static_cast<float2*>(PA)[idx] = make_float2(hi, lo);
+  } else {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      double a = 0.0;
+      for (int rr = 0; rr < RPW; ++rr) a += (double)val(w + rr * NW);
+      s = w == 0 ? a : s + a;
+    }
+    static_cast<double*>(PA)[idx] = s;
+  }
+}
+
+// one full warp: the b-partial of row y of tile txi in plane z
+template <int ACC>
+__device__ void recompute_pb(const GridDev& g, const float* __restrict__ u, void* PB, int txi, int z, int y) {
+  const int lane = threadIdx.x & 31;
+  const int gx0 = txi * kTX + 4 * lane;
+  float m[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    m[i] = (y < g.ny && gx0 + i < g.nx) ? __ldcg(u + ((size_t)z * g.ny + y) * g.px + gx0 + i) : 0.f;
+  AccA<ACC>::row_store(m, PB, ((size_t)txi * g.nz + z) * g.ny + y, lane == 0);
+}
+
+// ======================================================= shallow grids (nz <= kShallowMaxZ)
+// The whole column of a tile (all nz planes) is staged at once by one TMA box for u
+// (y halo of one row, x halo of 4) and one for C, signalled by one mbarrier.  Warp w
+// computes planes w, w + 8, ...; within a plane it walks the TY rows, so the a-partial
+// of each of its columns stays in registers (summed over rows in order) and no
+// cross-warp exchange or per-plane barrier is needed.  A persistent CTA that owns a
+// single tile keeps C resident and reloads only u.
+
+template <int TY>
+struct ShallowCfg {
+  static constexpr int NW = 8;
+  static constexpr int UROW = kUW * 4;                            // bytes of one staged u row
+  static constexpr int CROW = kTX * 4;
+  static constexpr int FLIPS = kLocalFlips * 16 + 16;
+  __host__ __device__ static int ubox(int nz) { return nz * (TY + 2) * UROW; }
+  __host__ __device__ static int ubox_al(int nz) { return (ubox(nz) + 127) / 128 * 128; }
+  __host__ __device__ static int cbox(int nz) { return nz * TY * CROW; }
+  __host__ __device__ static int smem(int nz) { return 128 + 128 + ubox_al(nz) + cbox(nz) + FLIPS; }
+};
+
+template <int TY>
+struct ShallowSmem {
+  uint64_t* bar;
+  float* u;
+  float* c;
+  int4* lflips;
+  int* nlf;
+  __device__ static ShallowSmem carve(unsigned char* raw, int nz) {
+    ShallowSmem m;
+    unsigned char* s = raw + ((128 - (smem_u32(raw) & 127)) & 127);
+    m.bar = reinterpret_cast<uint64_t*>(s);
+    m.u = reinterpret_cast<float*>(s + 128);
+    m.c = reinterpret_cast<float*>(s + 128 + ShallowCfg<TY>::ubox_al(nz));
+    m.lflips = reinterpret_cast<int4*>(s + 128 + ShallowCfg<TY>::ubox_al(nz) + ShallowCfg<TY>::cbox(nz));
+    m.nlf = reinterpret_cast<int*>(m.lflips + kLocalFlips);
+    return m;
+  }
+  __device__ void init_barriers() const {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+};
+
+// One shallow tile of one sweep, in two halves like the streaming tile: the issue half
+// starts the TMA loads (C too when load_c; otherwise C is already resident) and
+// gathers the flips; the run half waits for the loads (mbarrier phase parity `phase`,
+// toggled) and computes.  Every thread must call both.
+template <int TY>
+__device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
+                                                   int txi, int tyi, long long step, DevCtrl* __restrict__ ctrl,
+                                                   const DevSched& sched, const ShallowSmem<TY>& sm, bool load_c) {
+  using Cfg = ShallowCfg<TY>;
+  const int tid = threadIdx.x;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+  const int nz = g.nz;
+  if (tid == 0) {
+    fence_proxy_async_global();
+    mbar_expect_tx(sm.bar, Cfg::ubox(nz) + (load_c ? Cfg::cbox(nz) : 0));
+    tma_load_3d(sm.u, tm_u, x0 - kHaloX, y0 - 1, 0, sm.bar);
+    if (load_c) tma_load_3d(sm.c, tm_c, x0, y0, 0, sm.bar);
+    *sm.nlf = 0;
+  }
+  __syncthreads();
+  if (ctrl->inject_enabled) {
+    const long long i = step - ctrl->sched_t0;
+    if (i >= 0 && i < ctrl->sched_n) {
+      const int b = sched.off[i], e = sched.off[i + 1];
+      for (int k = b + tid; k < e; k += blockDim.x) {
+        const DevFlip f = sched.flips[k];
+        if (f.grid == g.gid && f.target == 0 && f.x >= x0 && f.x < x0 + kTX && f.x < g.nx && f.y >= y0 &&
+            f.y < y0 + TY && f.y < g.ny && f.z >= 0 && f.z < nz && f.x >= 0 && f.y >= 0) {
+          const int j = atomicAdd(sm.nlf, 1);
+          if (j < kLocalFlips) sm.lflips[j] = make_int4(f.x, f.y, f.z, f.bit & 31);
+          else set_status(ctrl, kStFlipOverflow);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int TY, bool PROT, int ACC>
+__device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __restrict__ uout, int txi, int tyi,
+                                                 DevCtrl* __restrict__ ctrl, const ShallowSmem<TY>& sm,
+                                                 unsigned& phase, int pbuf) {
+  constexpr int NW = ShallowCfg<TY>::NW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+  const int nz = g.nz;
+  mbar_wait(sm.bar, phase, ctrl);
+  phase ^= 1u;
+  const int nflip = min(*sm.nlf, kLocalFlips);
+  void* PA = pbuf ? g.PA2 : g.PA;
+  void* PB = pbuf ? g.PB2 : g.PB;
+  const int gx0 = x0 + 4 * lane;
+  const int last = g.nx - 1 - gx0;
+  constexpr int PLANE = (TY + 2) * kUW;
+  for (int z = warp; z < nz; z += NW) {
+    const float* Uz = sm.u + z * PLANE;
+    const float* Ub = z > 0 ? Uz - PLANE : Uz;
+    const float* Ut = z + 1 < nz ? Uz + PLANE : Uz;
+    const float* Cz = sm.c + z * TY * kTX;
+    AccA<ACC> acc;
+    if (PROT) acc.zero();
+#pragma unroll 4
+    for (int r = 0; r < TY; ++r) {
+      const int y = y0 + r;
+      const int o = (r + 1) * kUW + kHaloX + 4 * lane;
+      const float4 c = *reinterpret_cast<const float4*>(Uz + o);
+      float4 n = *reinterpret_cast<const float4*>(Uz + o - kUW);
+      float4 s = *reinterpret_cast<const float4*>(Uz + o + kUW);
+      const float4 b = *reinterpret_cast<const float4*>(Ub + o);
+      const float4 t = *reinterpret_cast<const float4*>(Ut + o);
+      const float4 cs = *reinterpret_cast<const float4*>(Cz + r * kTX + 4 * lane);
+      float wl = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float er = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (lane == 0) wl = Uz[o - 1];
+      if (lane == 31) er = Uz[o + 4];
+      if (y == 0) n = c;
+      if (y == g.ny - 1) s = c;
+      const float w0 = gx0 == 0 ? c.x : wl;
+      float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
+      if (last == 0) e0 = c.x;
+      if (last == 1) e1 = c.y;
+      if (last == 2) e2 = c.z;
+      if (last == 3) e3 = c.w;
+      float v[4];
+      v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
+      v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
+      v[2] = hs_update(g.k, c.z, c.y, e2, n.z, s.z, b.z, t.z, cs.z);
+      v[3] = hs_update(g.k, c.w, c.z, e3, n.w, s.w, b.w, t.w, cs.w);
+      if (nflip > 0) {
+        for (int f = 0; f < nflip; ++f) {
+          const int4 q = sm.lflips[f];
+          if (q.z == z && q.y == y) {
+            const int d = q.x - gx0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (d == i) v[i] = __int_as_float(__float_as_int(v[i]) ^ (1 << q.w));
+          }
+        }
+      }
+      const bool yv = y < g.ny;
+      float* dst = uout + ((size_t)z * g.ny + y) * g.px + gx0;
+      if (yv) {
+        if (last >= 3) {
+          *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (i <= last) dst[i] = v[i];
+        }
+      }
+      if (PROT) {
+        float m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
+        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.ny + y, yv && lane == 0);
+        acc.add(m);
+      }
+    }
+    if (PROT) acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
+  }
+  fence_proxy_async_global();
+  __syncthreads();
+}
+
+// a-partial of column x of shallow tile tyi in plane z, in the shallow tile's order
+template <int TY, int ACC>
+__device__ void recompute_pa_shallow(const GridDev& g, const float* __restrict__ u, void* PA, int tyi, int z, int x) {
+  const int y0 = tyi * TY;
+  auto val = [&](int r) -> float {
+    const int y = y0 + r;
+    return (y < g.ny && x < g.nx) ? __ldcg(u + ((size_t)z * g.ny + y) * g.px + x) : 0.f;
+  };
+  const size_t idx = ((size_t)tyi * g.nz + z) * g.pa_stride + x;
+  if (ACC == ABFT_ACC_FP32) {
+    float a = 0.f;
+    for (int r = 0; r < TY; ++r) a += val(r);
+    static_cast<float*>(PA)[idx] = a;
+  } else if (ACC == ABFT_ACC_TWOSUM) {
+    float h = 0.f, l = 0.f;
+    for (int r = 0; r < TY; ++r) acc2(h, l, val(r));
+    static_cast<float2*>(PA)[idx] = make_float2(h, l);
+  } else {
+    double a = 0.0;
+    for (int r = 0; r < TY; ++r) a += (double)val(r);
+    static_cast<double*>(PA)[idx] = a;
+  }
+}
+
+// ---------------------------------------------------------------- tile policies
+// The persistent and per-launch kernels are written once against these.
+
+template <int TY>
+struct StreamTiles {
+  static constexpr int NW = SweepCfg<TY>::NW;
+  SweepSmem<TY> sm;
+  unsigned seq;
+  __host__ static int smem_bytes(int) { return SweepCfg<TY>::SMEM; }
+  __device__ __forceinline__ void setup(unsigned char* raw, int) {
+    sm = SweepSmem<TY>::carve(raw);
+    seq = 0;
+    if (threadIdx.x == 0) sm.init_barriers();
+  }
+  __device__ __forceinline__ void issue(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g, int txi, int tyi,
+                        long long step, DevCtrl* ctrl, const DevSched& sched, bool) {
+    sweep_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, seq);
+  }
+  template <bool PROT, int ACC>
+  __device__ __forceinline__ void run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g, float* uout, int txi,
+                      int tyi, DevCtrl* ctrl, int pbuf) {
+    sweep_tile_run<TY, PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, sm, seq, pbuf);
+  }
+  template <int ACC>
+  __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
+    recompute_pa<TY, ACC>(g, u, PA, tyi, z, x);
+  }
+};
+
+template <int TY>
+struct ShallowTiles {
+  static constexpr int NW = ShallowCfg<TY>::NW;
+  ShallowSmem<TY> sm;
+  unsigned phase;
+  __host__ static int smem_bytes(int nz) { return ShallowCfg<TY>::smem(nz); }
+  __device__ __forceinline__ void setup(unsigned char* raw, int nz) {
+    sm = ShallowSmem<TY>::carve(raw, nz);
+    phase = 0;
+    if (threadIdx.x == 0) sm.init_barriers();
+  }
+  __device__ __forceinline__ void issue(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g, int txi, int tyi,
+                        long long step, DevCtrl* ctrl, const DevSched& sched, bool load_c) {
+    shallow_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, load_c);
+  }
+  template <bool PROT, int ACC>
+  __device__ __forceinline__ void run(const CUtensorMap*, const CUtensorMap*, const GridDev& g, float* uout, int txi, int tyi,
+                      DevCtrl* ctrl, int pbuf) {
+    shallow_tile_run<TY, PROT, ACC>(g, uout, txi, tyi, ctrl, sm, phase, pbuf);
+  }
+  template <int ACC>
+  __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
+    recompute_pa_shallow<TY, ACC>(g, u, PA, tyi, z, x);
+  }
+};
+
+}  // namespace abft

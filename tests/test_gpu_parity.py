@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 
 ONLINE, OFFLINE, NONE = 1, 2, 0
 # a handful of shapes spanning several tiles and ragged tails in x and y
-SHAPES = [(64, 64, 8), (200, 37, 5), (129, 17, 3), (300, 130, 2), (33, 1, 4), (1, 7, 1), (257, 64, 9)]
+SHAPES = [(64, 64, 8), (200, 37, 5), (129, 17, 3), (300, 130, 2), (33, 1, 4), (1, 7, 1), (257, 64, 9),
+          (150, 40, 20), (64, 33, 37)]
 
 
 @pytest.fixture(scope="module")
@@ -30,21 +31,24 @@ def value_tol(steps):
     return 1e-5 * max(1.0, steps / 100.0)
 
 
+@pytest.mark.parametrize("shallow", [0, 1])
 @pytest.mark.parametrize("tile_y", [8, 16, 32])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_one_sweep_matches_eq1(abi, orc, shape, tile_y):
-    with gpu_context(abi, [shape], [3], tile_y=tile_y) as ctx:
+def test_one_sweep_matches_eq1(abi, orc, shape, tile_y, shallow):
+    with gpu_context(abi, [shape], [3], tile_y=tile_y, shallow=shallow) as ctx:
         ctx.step(1, NONE)
         got = ctx.read(0)
     ref = oracle_run(orc, shape, 3, 1, orc.MODE_NONE)["u"]
     assert rel_err(got, ref) < 1e-6
 
 
+@pytest.mark.parametrize("shallow", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("acc", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5), (257, 64, 9)])
-def test_online_fault_free(abi, orc, shape, acc):
+@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5), (150, 40, 20)])
+def test_online_fault_free(abi, orc, shape, acc, persistent, shallow):
     steps = 100
-    with gpu_context(abi, [shape], [5], acc=acc) as ctx:
+    with gpu_context(abi, [shape], [5], acc=acc, persistent=persistent, shallow=shallow) as ctx:
         ctx.step(steps, ONLINE)
         got = ctx.read(0)
         ev = ctx.events()
@@ -54,11 +58,12 @@ def test_online_fault_free(abi, orc, shape, acc):
     assert rel_err(got, ref["u"]) < value_tol(steps)
 
 
-def test_online_one_flip_every_10_steps_64x64x8(abi, orc):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_online_one_flip_every_10_steps_64x64x8(abi, orc, persistent):
     """The small workload: 64x64x8, 100 sweeps, one seeded flip every 10 sweeps."""
     shape, steps = (64, 64, 8), 100
     flips = inputs.flips_periodic(shape, steps, 10, seed=0)
-    with gpu_context(abi, [shape], [0]) as ctx:
+    with gpu_context(abi, [shape], [0], persistent=persistent) as ctx:
         ctx.inject_list(flips)
         ctx.step(steps, ONLINE)
         got = ctx.read(0)
@@ -85,15 +90,16 @@ def test_online_each_bit(abi, orc, bit):
     assert rel_err(got, ref["u"]) < value_tol(steps) + (1e-3 if bit < 13 else 0)
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("case", ["two_by_two", "same_row", "same_col", "two_planes"])
-def test_online_multi_flip_patterns(abi, orc, case):
+def test_online_multi_flip_patterns(abi, orc, case, persistent):
     shape, steps = (200, 37, 5), 8
     e = {"two_by_two": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 20, 150, 28)],
          "same_row": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 5, 150, 28)],
          "same_col": [(3, 0, 2, 5, 7, 30), (3, 0, 2, 30, 7, 28)],
          "two_planes": [(3, 0, 1, 5, 7, 30), (3, 0, 4, 30, 199, 27)]}[case]
     flips = inputs.flip_list(e)
-    with gpu_context(abi, [shape], [2]) as ctx:
+    with gpu_context(abi, [shape], [2], persistent=persistent) as ctx:
         ctx.inject_list(flips)
         ctx.step(steps, ONLINE)
         got = ctx.read(0)
@@ -120,6 +126,75 @@ def test_offline_rollback_parity(abi, orc, shape):
     assert cnt["rollbacks"] == ref["n_rollbacks"] == 2
     # rolled-back windows are recomputed without faults; the surviving low-bit flip stays
     assert rel_err(got, ref["u"]) < value_tol(steps)
+
+
+@pytest.mark.parametrize("shape", [(300, 130, 6), (140, 70, 19)])
+@pytest.mark.parametrize("shallow", [0, 1])
+@pytest.mark.parametrize("mode", [ONLINE, NONE])
+def test_persistent_and_per_launch_paths_agree_bitwise(abi, mode, shallow, shape):
+    steps = 37
+    flips = inputs.flip_list([(3, 0, 2, 5, 7, 30), (11, 0, 4, 60, 100, 22), (11, 0, 1, 3, 3, 9),
+                              (20, 0, 5, 69, 139, 31), (20, 0, 5, 60, 17, 26)])
+    out = []
+    for persistent in (0, 1):
+        with gpu_context(abi, [shape], [12], persistent=persistent, shallow=shallow) as ctx:
+            ctx.inject_list(flips)
+            ctx.step(steps, mode)
+            out.append((ctx.read(0), sorted(map(tuple, ctx.events()[["step", "z", "y", "x", "kind"]].tolist()))))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+FIXUP_CASES = {
+    # flips in consecutive sweeps at neighbouring points: when sweep 5's flip is
+    # corrected, the repaired output of sweep 6 must still carry sweep 6's flip
+    "adjacent_sweeps": [(5, 0, 2, 10, 20, 29), (6, 0, 2, 10, 21, 27), (7, 0, 3, 10, 21, 30)],
+    "same_point_twice": [(5, 0, 1, 4, 4, 28), (6, 0, 1, 4, 4, 28)],
+    "lines_then_neighbour": [(8, 0, 2, 5, 7, 30), (8, 0, 2, 20, 150, 28), (9, 0, 2, 6, 100, 26),
+                             (9, 0, 1, 20, 149, 31)],
+    "plane_edges": [(4, 0, 0, 0, 0, 29), (4, 0, 5, 129, 299, 30), (5, 0, 0, 1, 0, 27)],
+    "last_sweep_of_launch": [(11, 0, 3, 33, 44, 29), (12, 0, 3, 33, 45, 28), (19, 0, 4, 100, 200, 25)],
+}
+
+
+@pytest.mark.parametrize("shallow", [0, 1])
+@pytest.mark.parametrize("case", sorted(FIXUP_CASES))
+def test_speculative_repair_cases(abi, orc, case, shallow):
+    """The persistent online kernel checks sweep s while running sweep s+1 and repairs
+    u^{s+1} when sweep s had to be corrected; results must equal checking after every
+    sweep (per-launch path, bitwise) and the oracle (events, values)."""
+    shape, steps = (300, 130, 6), 20
+    flips = inputs.flip_list(FIXUP_CASES[case])
+    out = []
+    for persistent in (0, 1):
+        with gpu_context(abi, [shape], [14], persistent=persistent, shallow=shallow) as ctx:
+            ctx.inject_list(flips)
+            ctx.step(12, ONLINE)
+            ctx.step(steps - 12, ONLINE)  # two launches: the second starts after a trailing check
+            out.append((ctx.read(0), ctx.events()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    key = lambda ev: sorted(map(tuple, ev[["step", "z", "y", "x", "kind"]].tolist()))
+    assert key(out[0][1]) == key(out[1][1])
+    ref = oracle_run(orc, shape, 14, steps, orc.MODE_ONLINE, flips)
+    g, o = compare_events(out[1][1], ref)
+    assert g == o and len(o) >= 1
+    assert rel_err(out[1][0], ref["u"]) < 1e-5
+
+
+def test_mixed_modes_continue_consistently(abi, orc):
+    """Unprotected, online and offline sweeps interleaved on one context follow the
+    same trajectory as the oracle's single run."""
+    shape = (130, 70, 5)
+    with gpu_context(abi, [shape], [13]) as ctx:
+        ctx.step(5, NONE)
+        ctx.step(7, ONLINE)
+        ctx.step(20, OFFLINE)
+        ctx.step(3, NONE)
+        ctx.step(4, ONLINE)
+        got = ctx.read(0)
+        assert len(ctx.events()) == 0
+    ref = oracle_run(orc, shape, 13, 39, orc.MODE_NONE)
+    assert rel_err(got, ref["u"]) < 1e-5
 
 
 def test_offline_fault_free_equals_unprotected(abi):
