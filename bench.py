@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                    help="grid shape for --profile captures (default 512 512 8)")
     p.add_argument("--sweeps", type=int, default=None, help="sweeps per job for --profile captures")
+    p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                   help="abft_options field for --profile captures (e.g. tile_y=16)")
     return p.parse_args()
 
 
@@ -294,9 +296,10 @@ def run_profile(args, local):
     abi.lib(build_if_missing=True)
     temp, power = inputs.grid_inputs(*SHAPE, seed=1)
     co = inputs.hotspot_coeffs(*SHAPE)
-    prot = abi.Context([SHAPE], [temp], [power], [co])
+    opts = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
+    prot = abi.Context([SHAPE], [temp], [power], [co], **opts)
     prot.inject(1, RATE, 0xFFFFFFFF)
-    plain = abi.Context([SHAPE], [temp], [power], [co])
+    plain = abi.Context([SHAPE], [temp], [power], [co], **opts)
     for _ in range(args.warmup):
         prot.step(SWEEPS, abi.MODE_ONLINE)
         plain.step(SWEEPS, abi.MODE_NONE)

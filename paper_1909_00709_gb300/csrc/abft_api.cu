@@ -397,9 +397,10 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
       q = c;
     }
     // zero the per-sweep fail counters and the barrier arrival count (contiguous)
-    static_assert(offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, fails) + 3 * sizeof(unsigned),
-                  "fails[] and bar[0] must be contiguous");
-    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned), ctx->stream));
+    static_assert(offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, fails) + 4 * sizeof(unsigned),
+                  "fails[] and bar must be contiguous");
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned) + sizeof(unsigned long long),
+                       ctx->stream));
     int blocks = 0;
     CK(run(ctx, prot ? kKPersistProt : kKPersistPlain, [&] {
       return launch_persistent(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], ctx->step, (int)n, c, p, q, prot, &blocks);
@@ -828,7 +829,9 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
       if (s) return s;
       continue;
     }
-    if (ctx->opt.persistent && covered > 0) {
+    bool persist = ctx->opt.persistent && covered > 0;
+    for (int gi = 0; gi < ctx->n && persist; ++gi) persist = persistent_fits(ctx->g[gi], mode == ABFT_MODE_ONLINE);
+    if (persist) {
       s = persistent_all(ctx, covered, mode);
       if (s) return s;
       continue;

@@ -17,7 +17,8 @@ constexpr int kFCap = 64;         // failing entries kept per plane and vector
 constexpr int kLocalFlips = 32;   // flips a tile can apply in one sweep
 constexpr int kSchedSteps = 4096; // sweeps covered by one uploaded schedule chunk
 constexpr int kShallowMaxZ = 16;  // grids this shallow are swept with whole-column tiles
-constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side wait loop
+constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side mbarrier wait loop
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // grid barrier wait bound
 
 // sticky device status bits
 enum : unsigned {
@@ -54,8 +55,8 @@ struct DevGridCtrl {
   unsigned int done_aux;
   unsigned int pad;
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
-  unsigned int bar[2];      // grid barrier of the persistent kernel: arrivals, generation
   unsigned int pad2;
+  unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
 };
@@ -113,6 +114,7 @@ cudaError_t launch_compare(const Launch& L, const GridDev& g, const double* ap, 
                            const double* a, const double* b);
 cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
                               long long step0, int n_steps, int first_in, int p, int q, bool prot, int* blocks);
+bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);
 

@@ -3,6 +3,8 @@
 //
 // Predictions, comparisons and corrections run in FP64; the per-tile partial sums
 // of the sweep are reduced across tiles in a fixed order.
+#include <algorithm>
+
 #include "check_dev.cuh"
 
 namespace abft {
@@ -18,8 +20,12 @@ template <int ACC>
 __global__ void __launch_bounds__(kCheckThreads)
     k_check_online(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
   const int n = g.nz * (g.nx + g.ny);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    check_entry<ACC>(g, in, out, i);
+  __shared__ CheckShared sh;
+  for (int base = blockIdx.x * 32; base < n; base += gridDim.x * 32) {  // 32 entries per block round
+    CheckRound<ACC> c;
+    c.load(g, in, 0, base, n);
+    c.finish(g, out, 0, nullptr, sh);
+  }
   double* Aout = g.A[out];
   double* Bout = g.B[out];
   const float* uin = g.u[in];
@@ -140,15 +146,15 @@ __global__ void k_checksum_b(const GridDev g, const float* u, double* B) {
 
 // ------------------------------------------------------------------ launchers
 
-static int check_blocks(const GridDev& g) {
-  const long long n = (long long)g.nz * (g.nx + g.ny);
+static int check_blocks(const GridDev& g, int lanes = 1) {
+  const long long n = (long long)g.nz * (g.nx + g.ny) * lanes;
   long long b = (n + kCheckThreads - 1) / kCheckThreads;
   if (b > 65535) b = 65535;
   return (int)(b < 1 ? 1 : b);
 }
 
 cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out) {
-  const int blocks = check_blocks(g);
+  const int blocks = (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + 31) / 32, 65535);
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: k_check_online<ABFT_ACC_TWOSUM><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
     case ABFT_ACC_FP64: k_check_online<ABFT_ACC_FP64><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;

@@ -19,24 +19,70 @@ __device__ __forceinline__ double load_partial(const void* p, size_t i) {
   return __ldcg(static_cast<const double*>(p) + i);
 }
 
-// Sum of n partials p[i0 + k*stride], k = 0..n-1, in order; loads are issued in
-// batches of 8 so that their latencies overlap.
+// The canonical cross-tile sum of n partials p[i0 + k*stride]: eight interleaved
+// lanes j accumulate p_k over k = j, j+8, j+16, ... (ascending), then the lanes are
+// combined in order 0..7.  FP32 and TwoSum partials are accumulated as compensated
+// FP32 pairs (hi, lo) with TwoSum (error about n u^2, below FP64 rounding of the
+// total here, and at FP32 speed: GB300's FP64 rate is a small fraction of its FP32
+// rate); the pair is widened once, hi + lo in FP64.  The FP64 variant sums in FP64.
+// Every path (one thread per entry, or eight cooperating warps) evaluates exactly
+// this, so results agree bit for bit.
+constexpr int kLanes = 8;
+
 template <int ACC>
-__device__ __forceinline__ double sum_partials(const void* p, size_t i0, size_t stride, int n) {
-  double s = 0.0;
-  int k = 0;
-  for (; k + 8 <= n; k += 8) {
-    double v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = load_partial<ACC>(p, i0 + (size_t)(k + j) * stride);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s += v[j];
-  }
-  for (; k < n; ++k) s += load_partial<ACC>(p, i0 + (size_t)k * stride);
-  return s;
+struct PartialType { using T = float; };
+template <>
+struct PartialType<ABFT_ACC_TWOSUM> { using T = float2; };
+template <>
+struct PartialType<ABFT_ACC_FP64> { using T = double; };
+
+template <int ACC>
+__device__ __forceinline__ typename PartialType<ACC>::T load_raw(const void* p, size_t i) {
+  return __ldcg(static_cast<const typename PartialType<ACC>::T*>(p) + i);
 }
 
-// a[z][x] of the last protected sweep: the tiles' partials summed in tile order
+// running sum of one lane: (hi, lo) FP32 pair, or d for the FP64 variant
+struct LaneSum {
+  float hi = 0.f, lo = 0.f;
+  double d = 0.0;
+  __device__ __forceinline__ void add(float v) { acc2(hi, lo, v); }
+  __device__ __forceinline__ void add(float2 v) {
+    acc2(hi, lo, v.x);
+    lo += v.y;
+  }
+  __device__ __forceinline__ void add(double v) { d = __dadd_rn(d, v); }
+  // lane combination: (this) += other, in the same arithmetic
+  template <int ACC>
+  __device__ __forceinline__ void merge(const LaneSum& o) {
+    if (ACC == ABFT_ACC_FP64) {
+      d = __dadd_rn(d, o.d);
+    } else {
+      acc2(hi, lo, o.hi);
+      lo += o.lo;
+    }
+  }
+  template <int ACC>
+  __device__ __forceinline__ double total() const {
+    return ACC == ABFT_ACC_FP64 ? d : __dadd_rn((double)hi, (double)lo);
+  }
+};
+
+template <int ACC>
+__device__ __forceinline__ LaneSum lane_sum(const void* p, size_t i0, size_t stride, int n, int j) {
+  LaneSum t;
+  for (int k = j; k < n; k += kLanes) t.add(load_raw<ACC>(p, i0 + (size_t)k * stride));
+  return t;
+}
+
+template <int ACC>
+__device__ __forceinline__ double sum_partials(const void* p, size_t i0, size_t stride, int n) {
+  LaneSum s = lane_sum<ACC>(p, i0, stride, n, 0);
+#pragma unroll
+  for (int j = 1; j < kLanes; ++j) s.merge<ACC>(lane_sum<ACC>(p, i0, stride, n, j));
+  return s.total<ACC>();
+}
+
+// a[z][x] of the last protected sweep: the tiles' partials summed in the canonical order
 template <int ACC>
 __device__ __forceinline__ double reduce_a(const GridDev& g, int z, int x, int pbuf = 0) {
   return sum_partials<ACC>(pbuf ? g.PA2 : g.PA, (size_t)z * g.pa_stride + x, (size_t)g.nz * g.pa_stride, g.nty);
@@ -47,39 +93,59 @@ __device__ __forceinline__ double reduce_b(const GridDev& g, int z, int y, int p
   return sum_partials<ACC>(pbuf ? g.PB2 : g.PB, (size_t)z * g.ny + y, (size_t)g.nz * g.ny, g.ntx);
 }
 
-// Theorem 1 for the clamped 7-point set, one entry of a (Eq. 4): shifts along x and z
-// are clamped index shifts of the vector; the two y-shifts add a to itself plus the
-// boundary term (cn - cs) * (u[z][0][x] - u[z][ny-1][x]), zero when cn == cs.
+// Theorem 1 for the clamped 7-point set (Eq. 4 for a, Eq. 5 for b): shifts along the
+// surviving in-plane axis and along z are clamped index shifts of the vector; the two
+// shifts along the collapsed axis add the entry to itself plus the boundary term
+// (w_- - w_+) * (u at the first minus u at the last index), zero for equal weights.
+// Evaluated with explicit FP64 roundings in a fixed order: c the checksum of C, v0 the
+// entry, v1/v2 its clamped neighbours along the surviving in-plane axis, v3/v4 along z,
+// w0 the summed weight of the centre and the collapsed-axis pair.
+__device__ __forceinline__ double interp(double c, double v0, double v1, double v2, double v3, double v4,
+                                         double w0, double w1, double w2, double w3, double w4, double edge) {
+  double p = __fma_rn(w0, v0, c);
+  p = __fma_rn(w1, v1, p);
+  p = __fma_rn(w2, v2, p);
+  p = __fma_rn(w3, v3, p);
+  p = __fma_rn(w4, v4, p);
+  return __dadd_rn(p, edge);
+}
+
+__device__ __forceinline__ double weight_sum3(float a, float b, float c) {
+  return __dadd_rn(__dadd_rn((double)a, (double)b), (double)c);
+}
+
+__device__ __forceinline__ double edge_term(float wm, float wp, float first, float last) {
+  return __dmul_rn(__dadd_rn((double)wm, -(double)wp), __dadd_rn((double)first, -(double)last));
+}
+
 __device__ __forceinline__ double predict_a(const GridDev& g, const double* A, const float* u, int z, int x) {
   const int nx = g.nx;
   const int xm = x > 0 ? x - 1 : 0, xp = x < nx - 1 ? x + 1 : nx - 1;
   const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
   const Coef& k = g.k;
-  double p = g.cx[(size_t)z * nx + x] + ((double)k.cc + (double)k.cn + (double)k.cs) * __ldcg(A + (size_t)z * nx + x) +
-             (double)k.cw * __ldcg(A + (size_t)z * nx + xm) + (double)k.ce * __ldcg(A + (size_t)z * nx + xp) +
-             (double)k.cb * __ldcg(A + (size_t)zm * nx + x) + (double)k.ct * __ldcg(A + (size_t)zp * nx + x);
+  double edge = 0.0;
   if (u != nullptr && k.cn != k.cs) {
     const size_t pl = (size_t)z * g.ny * g.px;
-    p += ((double)k.cn - (double)k.cs) *
-         ((double)__ldcg(u + pl + x) - (double)__ldcg(u + pl + (size_t)(g.ny - 1) * g.px + x));
+    edge = edge_term(k.cn, k.cs, __ldcg(u + pl + x), __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + x));
   }
-  return p;
+  return interp(g.cx[(size_t)z * nx + x], __ldcg(A + (size_t)z * nx + x), __ldcg(A + (size_t)z * nx + xm),
+                __ldcg(A + (size_t)z * nx + xp), __ldcg(A + (size_t)zm * nx + x), __ldcg(A + (size_t)zp * nx + x),
+                weight_sum3(k.cc, k.cn, k.cs), k.cw, k.ce, k.cb, k.ct, edge);
 }
 
-// Eq. (5): the same along y for the column checksum b
 __device__ __forceinline__ double predict_b(const GridDev& g, const double* B, const float* u, int z, int y) {
   const int ny = g.ny;
   const int ym = y > 0 ? y - 1 : 0, yp = y < ny - 1 ? y + 1 : ny - 1;
   const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
   const Coef& k = g.k;
-  double p = g.cy[(size_t)z * ny + y] + ((double)k.cc + (double)k.cw + (double)k.ce) * __ldcg(B + (size_t)z * ny + y) +
-             (double)k.cn * __ldcg(B + (size_t)z * ny + ym) + (double)k.cs * __ldcg(B + (size_t)z * ny + yp) +
-             (double)k.cb * __ldcg(B + (size_t)zm * ny + y) + (double)k.ct * __ldcg(B + (size_t)zp * ny + y);
+  double edge = 0.0;
   if (u != nullptr && k.cw != k.ce) {
     const size_t row = ((size_t)z * g.ny + y) * g.px;
-    p += ((double)k.cw - (double)k.ce) * ((double)__ldcg(u + row) - (double)__ldcg(u + row + g.nx - 1));
+    edge = edge_term(k.cw, k.ce, __ldcg(u + row), __ldcg(u + row + g.nx - 1));
   }
-  return p;
+  return interp(g.cy[(size_t)z * ny + y], __ldcg(B + (size_t)z * ny + y), __ldcg(B + (size_t)z * ny + ym),
+                __ldcg(B + (size_t)z * ny + yp), __ldcg(B + (size_t)zm * ny + y), __ldcg(B + (size_t)zp * ny + y),
+                weight_sum3(k.cc, k.cw, k.ce), k.cn, k.cs, k.cb, k.ct, edge);
 }
 
 // Sec. 3.4: flag unless |pred - comp| <= eps |comp| (NaN and Inf are flagged)
@@ -275,5 +341,158 @@ __device__ __forceinline__ void check_entry(const GridDev& g, int in, int out, i
     if (fails(p, s, g.eps)) append_fail(g, z, 1, y, any);
   }
 }
+
+// ------------------------------------------------------------ block check rounds
+// One round of the online check (Sec. 3) by a block of 8 warps: 32 consecutive
+// entries, entry e = base + lane.  Warp w is lane w of the canonical sum: it loads the
+// partials k = w, w+8, ... of its lane's entry (coalesced across the warp) and one
+// interpolation input (w = 0..4 the entry and its neighbours, 5 the constant-term
+// checksum, 6/7 the boundary-term values).  finish() meets the eight warp sums in
+// shared memory and warp 0 adds them in order, interpolates and tests.  load()
+// before a sweep and finish() after it hide the load latency.  The arithmetic is that
+// of sum_partials and predict_a/b, so results are bit-identical to check_entry.
+struct CheckShared {
+  float th[kLanes][32], tl[kLanes][32];
+  double td[kLanes][32];
+  double p[kLanes][32];
+};
+
+template <int ACC>
+struct CheckRound {
+  static constexpr int PF = 8;  // prefetched partials per warp lane (more are loaded in finish)
+  typename PartialType<ACC>::T pv[PF];
+  double pin;
+  int e;  // this thread's entry, -1 if beyond the range
+
+  // where entry e's partials live
+  __device__ __forceinline__ static void partials_of(const GridDev& g, int e, int pbuf, const void** P, size_t* i0,
+                                                     size_t* stride, int* n) {
+    const int na = g.nz * g.nx;
+    if (e < na) {
+      const int z = e / g.nx, x = e - z * g.nx;
+      *P = pbuf ? g.PA2 : g.PA;
+      *i0 = (size_t)z * g.pa_stride + x;
+      *stride = (size_t)g.nz * g.pa_stride;
+      *n = g.nty;
+    } else {
+      const int b = e - na;
+      const int z = b / g.ny, y = b - z * g.ny;
+      *P = pbuf ? g.PB2 : g.PB;
+      *i0 = (size_t)z * g.ny + y;
+      *stride = (size_t)g.nz * g.ny;
+      *n = g.ntx;
+    }
+  }
+
+  __device__ __forceinline__ void load(const GridDev& g, int in, int pbuf, int base, int end) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    e = base + lane < end ? base + lane : -1;
+    pin = 0.0;
+    if (e < 0) return;
+    const int na = g.nz * g.nx;
+    if (e < na) {
+      const int z = e / g.nx, x = e - z * g.nx;
+      const int xm = x > 0 ? x - 1 : 0, xp = x < g.nx - 1 ? x + 1 : g.nx - 1;
+      const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+      const double* A = g.A[in];
+      const size_t pl = (size_t)z * g.ny * g.px;
+      switch (w) {
+        case 0: pin = __ldcg(A + (size_t)z * g.nx + x); break;
+        case 1: pin = __ldcg(A + (size_t)z * g.nx + xm); break;
+        case 2: pin = __ldcg(A + (size_t)z * g.nx + xp); break;
+        case 3: pin = __ldcg(A + (size_t)zm * g.nx + x); break;
+        case 4: pin = __ldcg(A + (size_t)zp * g.nx + x); break;
+        case 5: pin = g.cx[(size_t)z * g.nx + x]; break;
+        case 6: if (g.k.cn != g.k.cs) pin = (double)__ldcg(g.u[in] + pl + x); break;
+        default: if (g.k.cn != g.k.cs) pin = (double)__ldcg(g.u[in] + pl + (size_t)(g.ny - 1) * g.px + x); break;
+      }
+    } else {
+      const int b = e - na;
+      const int z = b / g.ny, y = b - z * g.ny;
+      const int ym = y > 0 ? y - 1 : 0, yp = y < g.ny - 1 ? y + 1 : g.ny - 1;
+      const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+      const double* B = g.B[in];
+      const size_t row = ((size_t)z * g.ny + y) * g.px;
+      switch (w) {
+        case 0: pin = __ldcg(B + (size_t)z * g.ny + y); break;
+        case 1: pin = __ldcg(B + (size_t)z * g.ny + ym); break;
+        case 2: pin = __ldcg(B + (size_t)z * g.ny + yp); break;
+        case 3: pin = __ldcg(B + (size_t)zm * g.ny + y); break;
+        case 4: pin = __ldcg(B + (size_t)zp * g.ny + y); break;
+        case 5: pin = g.cy[(size_t)z * g.ny + y]; break;
+        case 6: if (g.k.cw != g.k.ce) pin = (double)__ldcg(g.u[in] + row); break;
+        default: if (g.k.cw != g.k.ce) pin = (double)__ldcg(g.u[in] + row + g.nx - 1); break;
+      }
+    }
+    const void* P;
+    size_t i0, stride;
+    int n;
+    partials_of(g, e, pbuf, &P, &i0, &stride, &n);
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int k = w + kLanes * q;
+      if (k < n) pv[q] = load_raw<ACC>(P, i0 + (size_t)k * stride);
+    }
+  }
+
+  // every thread of the block must call this
+  __device__ __forceinline__ void finish(const GridDev& g, int out, int pbuf, unsigned* any, CheckShared& sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    LaneSum t;
+    if (e >= 0) {
+      const void* P;
+      size_t i0, stride;
+      int n;
+      partials_of(g, e, pbuf, &P, &i0, &stride, &n);
+#pragma unroll
+      for (int q = 0; q < PF; ++q)
+        if (w + kLanes * q < n) t.add(pv[q]);
+      for (int k = w + kLanes * PF; k < n; k += kLanes) t.add(load_raw<ACC>(P, i0 + (size_t)k * stride));
+    }
+    sh.th[w][lane] = t.hi;
+    sh.tl[w][lane] = t.lo;
+    sh.td[w][lane] = t.d;
+    sh.p[w][lane] = pin;
+    __syncthreads();
+    if (w == 0 && e >= 0) {
+      LaneSum acc;
+      acc.hi = sh.th[0][lane];
+      acc.lo = sh.tl[0][lane];
+      acc.d = sh.td[0][lane];
+#pragma unroll
+      for (int q = 1; q < kLanes; ++q) {
+        LaneSum o;
+        o.hi = sh.th[q][lane];
+        o.lo = sh.tl[q][lane];
+        o.d = sh.td[q][lane];
+        acc.merge<ACC>(o);
+      }
+      const double s = acc.total<ACC>();
+      const double* v = &sh.p[0][lane];
+      const int st = 32;  // stride between the lanes' inputs in sh.p
+      const Coef& k = g.k;
+      const int na = g.nz * g.nx;
+      if (e < na) {
+        const int z = e / g.nx, x = e - z * g.nx;
+        const double edge = k.cn != k.cs ? edge_term(k.cn, k.cs, (float)v[6 * st], (float)v[7 * st]) : 0.0;
+        const double p = interp(v[5 * st], v[0], v[st], v[2 * st], v[3 * st], v[4 * st], weight_sum3(k.cc, k.cn, k.cs),
+                                k.cw, k.ce, k.cb, k.ct, edge);
+        g.A[out][e] = s;
+        g.AP[0][e] = p;
+        if (fails(p, s, g.eps)) append_fail(g, z, 0, x, any);
+      } else {
+        const int b = e - na;
+        const int z = b / g.ny, y = b - z * g.ny;
+        const double edge = k.cw != k.ce ? edge_term(k.cw, k.ce, (float)v[6 * st], (float)v[7 * st]) : 0.0;
+        const double p = interp(v[5 * st], v[0], v[st], v[2 * st], v[3 * st], v[4 * st], weight_sum3(k.cc, k.cw, k.ce),
+                                k.cn, k.cs, k.cb, k.ct, edge);
+        g.B[out][b] = s;
+        g.BP[0][b] = p;
+        if (fails(p, s, g.eps)) append_fail(g, z, 1, y, any);
+      }
+    }
+    __syncthreads();
+  }
+};
 
 }  // namespace abft

@@ -140,32 +140,39 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier of a cooperative launch: count[0] arrivals, count[1] generation.
-// The wait is bounded; on timeout the status word records it and every later
-// barrier returns at once, so a broken launch ends instead of hanging.  Returns
-// false once the launch is poisoned.  All threads of every block must call it.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, DevCtrl* ctrl) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch on a monotonic arrival counter (zeroed
+// before the launch): arrival a waits until the count reaches the next multiple of
+// the grid size.  One release fetch-add and acquire polls.  The wait is bounded in
+// time; on timeout, or when another CTA has already timed out, the status word
+// records it and the barrier returns false, so a broken launch winds down instead
+// of hanging.  All threads of every block must call it.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, DevCtrl* ctrl) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = (ld_acquire_u32(&ctrl->status) & kStTimeout) == 0;
-    if (ok) {
-      const unsigned gen = ld_acquire_u32(&count[1]);
-      __threadfence();
-      const unsigned arrived = atomicAdd(&count[0], 1u) + 1u;
-      if (arrived == gridDim.x * gridDim.y * gridDim.z) {
-        atomicExch(&count[0], 0u);
-        __threadfence();
-        st_release_u32(&count[1], gen + 1u);
-      } else {
-        unsigned spins = 0;
-        while (ld_acquire_u32(&count[1]) == gen) {
-          if (++spins > kSpinLimit || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
-            set_status(ctrl, kStTimeout);
-            ok = 0;
-            break;
-          }
-          __nanosleep(20);
+    int ok = 1;
+    const unsigned long long n = gridDim.x * gridDim.y * gridDim.z;
+    unsigned long long a;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(a) : "l"(count) : "memory");
+    const unsigned long long target = (a / n + 1) * n;
+    unsigned long long seen;
+    unsigned long long t0 = 0;
+    for (unsigned spins = 0;; ++spins) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
+      if (seen >= target) break;
+      if ((spins & 1023u) == 1023u) {
+        const unsigned long long t = globaltimer_ns();
+        if (t0 == 0) t0 = t;
+        if (t - t0 > kBarrierTimeoutNs || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
+          set_status(ctrl, kStTimeout);
+          ok = 0;
+          break;
         }
       }
     }

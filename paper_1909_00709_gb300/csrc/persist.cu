@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256, 2)
       tiles.template run<false, ABFT_ACC_FP32>(&a.tm_u[in], &a.tm_c, g, g.u[out], tile % g.ntx, tile / g.ntx, ctrl,
                                                0);
     }
-    ok = grid_barrier(g.gc->bar, ctrl);
+    ok = grid_barrier(&g.gc->bar, ctrl);
   }
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
 }
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(256, 2)
                      const DevSched sched) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ResolveSmem rs;
+  __shared__ CheckShared csh;
   const GridDev& g = a.g;
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
@@ -164,11 +165,12 @@ __global__ void __launch_bounds__(256, 2)
     prefetch_tensormap(&a.tm_c);
   }
   __syncthreads();
-  unsigned* bar = g.gc->bar;
+  unsigned long long* bar = &g.gc->bar;
   const int ntiles = g.ntx * g.nty;
   const int n_entries = g.nz * (g.nx + g.ny);
   const int first_tile = blockIdx.x;
   const bool resident_c = (int)gridDim.x >= ntiles;
+  static_assert(256 == 32 * kLanes, "one warp per lane of the canonical sum");
   bool ok = true;
   for (int k = 0; k <= a.n_steps && ok; ++k) {
     const long long s = a.step0 + k;
@@ -180,17 +182,30 @@ __global__ void __launch_bounds__(256, 2)
     if (sweep && first_tile < ntiles)
       tiles.issue(&a.tm_u[cur], &a.tm_c, g, first_tile % g.ntx, first_tile / g.ntx, s, ctrl, sched,
                   !resident_c || k == 0);
-    // b. check u^s against the interpolation from a^{s-1}, b^{s-1}
+    // b. check u^s against the interpolation from a^{s-1}, b^{s-1}: this CTA's entries
+    //    [e0, e1) in rounds of 32; the first round's loads are issued now and consumed
+    //    after the sweep, so their latency hides under it
     unsigned* any = &g.gc->fails[s % 3];
-    if (check)
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_entries; i += gridDim.x * blockDim.x)
-        check_entry<ACC>(g, prv, cur, i, any, pb_cur);
+    const int e0 = (int)((long long)n_entries * blockIdx.x / gridDim.x);
+    const int e1 = (int)((long long)n_entries * (blockIdx.x + 1) / gridDim.x);
+    CheckRound<ACC> pre;
+    if (check) pre.load(g, prv, pb_cur, e0, e1);
     // c. sweep u^s -> u^{s+1}
     if (sweep) {
       for (int tile = first_tile; tile < ntiles; tile += gridDim.x) {
         if (tile != first_tile)
           tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, true);
         tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl, pb_nxt);
+      }
+    }
+    if (check) {
+      pre.finish(g, cur, pb_cur, any, csh);
+      for (int base = e0 + 32; base < e1; base += 64) {  // remaining rounds, two at a time
+        CheckRound<ACC> c0, c1;
+        c0.load(g, prv, pb_cur, base, e1);
+        c1.load(g, prv, pb_cur, base + 32, e1);
+        c0.finish(g, cur, pb_cur, any, csh);
+        c1.finish(g, cur, pb_cur, any, csh);
       }
     }
     // d.
@@ -250,6 +265,29 @@ static cudaError_t launch_persist_ty(const Launch& L, const PersistArgs& a, bool
     case ABFT_ACC_TWOSUM: return launch_persist_t<Tiles, TY, true, ABFT_ACC_TWOSUM>(L, a, blocks);
     case ABFT_ACC_FP64: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP64>(L, a, blocks);
     default: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP32>(L, a, blocks);
+  }
+}
+
+// Whether the persistent kernel for this grid would give every CTA a single tile
+// (the case it is built for; larger grids keep one launch per sweep).
+template <class Tiles, int TY>
+static bool fits_t(const GridDev& g, bool prot) {
+  const void* kern = prot ? (const void*)k_persist_online<Tiles, TY, ABFT_ACC_FP32> : (const void*)k_persist_plain<Tiles>;
+  const int smem = Tiles::smem_bytes(g.nz);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+  int per_sm = 0, sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  return (long long)g.ntx * g.nty <= (long long)per_sm * sms;
+}
+
+bool persistent_fits(const GridDev& g, bool prot) {
+  if (g.shallow) return g.ty == 8 ? fits_t<ShallowTiles<8>, 8>(g, prot) : fits_t<ShallowTiles<16>, 16>(g, prot);
+  switch (g.ty) {
+    case 8: return fits_t<StreamTiles<8>, 8>(g, prot);
+    case 16: return fits_t<StreamTiles<16>, 16>(g, prot);
+    default: return fits_t<StreamTiles<32>, 32>(g, prot);
   }
 }
 

@@ -403,6 +403,77 @@ __device__ void recompute_pb(const GridDev& g, const float* __restrict__ u, void
   AccA<ACC>::row_store(m, PB, ((size_t)txi * g.nz + z) * g.ny + y, lane == 0);
 }
 
+// --------------------------------------------- multi-row reduction of row partials
+// R rows (R = 8 or 16) held by every lane of a warp, one lane-partial per row, are
+// reduced to R row totals with log2(R) halving exchanges (offsets 16, 8, ...) and
+// butterfly exchanges for the remaining offsets.  Every stage pairs lanes l and l^o,
+// the same pairs, in the same stage order, as the per-row butterfly of row_store, and
+// each stage's addition is commutative, so every row total is bit-identical to
+// row_store's.  Lane l ends holding row (l >> (5 - log2 R)).
+template <int ACC>
+struct RowPart;
+template <>
+struct RowPart<ABFT_ACC_FP32> {
+  using T = float;
+  __device__ static T of(const float (&m)[4]) { return ((m[0] + m[1]) + m[2]) + m[3]; }
+  __device__ static T comb(T a, T b) { return a + b; }
+  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<float*>(PB)[i] = v; }
+};
+template <>
+struct RowPart<ABFT_ACC_TWOSUM> {
+  using T = float2;
+  __device__ static T of(const float (&m)[4]) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc2(hi, lo, m[i]);
+    return make_float2(hi, lo);
+  }
+  __device__ static T comb(T a, T b) {  // as warp_sum2: two_sum(a.hi, b.hi), lo = a.lo + b.lo + e
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return make_float2(s, a.y + b.y + e);
+  }
+  __device__ static T shfl(T v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+  }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<float2*>(PB)[i] = v; }
+};
+template <>
+struct RowPart<ABFT_ACC_FP64> {
+  using T = double;
+  __device__ static T of(const float (&m)[4]) { return (((double)m[0] + (double)m[1]) + (double)m[2]) + (double)m[3]; }
+  __device__ static T comb(T a, T b) { return a + b; }
+  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<double*>(PB)[i] = v; }
+};
+
+template <int ACC, int R>
+__device__ __forceinline__ typename RowPart<ACC>::T reduce_rows(typename RowPart<ACC>::T (&v)[R], int lane) {
+  using RP = RowPart<ACC>;
+  static_assert(R == 8 || R == 16, "row count");
+  constexpr int L = R == 8 ? 3 : 4;  // halving stages
+  int cnt = R;
+#pragma unroll
+  for (int st = 0; st < L; ++st) {
+    const int o = 16 >> st;
+    const bool up = (lane & o) != 0;  // keeps the upper half of its current rows
+    cnt >>= 1;
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      if (i < cnt) {
+        const typename RP::T send = up ? v[i] : v[i + cnt];
+        const typename RP::T keep = up ? v[i + cnt] : v[i];
+        v[i] = RP::comb(keep, RP::shfl(send, o));
+      }
+    }
+  }
+  typename RP::T t = v[0];
+#pragma unroll
+  for (int o = 16 >> L; o > 0; o >>= 1) t = RP::comb(t, RP::shfl(t, o));
+  return t;
+}
+
 // ======================================================= shallow grids (nz <= kShallowMaxZ)
 // The whole column of a tile (all nz planes) is staged at once by one TMA box for u
 // (y halo of one row, x halo of 4) and one for C, signalled by one mbarrier.  Warp w
@@ -507,7 +578,8 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
     const float* Cz = sm.c + z * TY * kTX;
     AccA<ACC> acc;
     if (PROT) acc.zero();
-#pragma unroll 4
+    typename RowPart<ACC>::T rp[TY];
+#pragma unroll
     for (int r = 0; r < TY; ++r) {
       const int y = y0 + r;
       const int o = (r + 1) * kUW + kHaloX + 4 * lane;
@@ -560,11 +632,17 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
         float m[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
-        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.ny + y, yv && lane == 0);
+        rp[r] = RowPart<ACC>::of(m);
         acc.add(m);
       }
     }
-    if (PROT) acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
+    if (PROT) {
+      acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
+      const typename RowPart<ACC>::T tot = reduce_rows<ACC, TY>(rp, lane);
+      constexpr int SH = TY == 8 ? 2 : 1;  // lane l holds row l >> SH
+      const int r = lane >> SH, y = y0 + r;
+      if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny) RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.ny + y, tot);
+    }
   }
   fence_proxy_async_global();
   __syncthreads();
