@@ -213,12 +213,17 @@ def run_ours(args, rank, world, local):
     events = prot.events()
     off_cnt = off.counters()
 
-    # dominant kernel: average launch duration from CUDA events on the launching stream
-    kt = prot.time_kernels(200, abi.MODE_ONLINE)
-    sweep_ms, sweep_n = kt["sweep_protected"]
-    sweep_avg_s = sweep_ms / sweep_n / 1e3
-    check_ms, check_n = kt["check_online"]
-    achieved = BYTES_PER_UPDATE * n_points() / sweep_avg_s / 1e9
+    # dominant kernel: average launch duration from CUDA events on the launching stream.
+    # A persistent launch runs many sweeps; its algorithmic bytes are 12 B per point and sweep.
+    timed_sweeps = 200
+    kt = prot.time_kernels(timed_sweeps, abi.MODE_ONLINE)
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    sweeps_per_launch = timed_sweeps / dom_n if dom.startswith("persistent") else 1
+    dom_avg_s = dom_ms / dom_n / 1e3
+    achieved = BYTES_PER_UPDATE * n_points() * sweeps_per_launch / dom_avg_s / 1e9
+    kernel_names = {"persistent_protected": "k_persist_online", "sweep_protected": "k_sweep<protected>",
+                    "check_online": "k_check_online"}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -274,9 +279,10 @@ def run_ours(args, rank, world, local):
                     "rollbacks": off_cnt["rollbacks"]},
         "events": {"corrected": int((events["kind"] == 1).sum()), "recomputed": int((events["kind"] == 2).sum())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_sweep<protected>",
-                     "avg_launch_us": sweep_avg_s * 1e6, "peak_source": peak_src,
-                     "check_kernel_avg_us": check_ms / max(check_n, 1) * 1e3},
+                     "frac": achieved / peak, "traffic": None, "kernel": kernel_names.get(dom, dom),
+                     "avg_launch_us": dom_avg_s * 1e6, "sweeps_per_launch": sweeps_per_launch,
+                     "us_per_sweep": dom_avg_s * 1e6 / sweeps_per_launch, "peak_source": peak_src,
+                     "note": "algorithmic 12 B per point-update; the 24 MB working set is L2-resident"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

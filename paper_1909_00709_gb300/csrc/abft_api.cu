@@ -85,9 +85,9 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     for (int k = 0; k < 3; ++k) { p.A[k] = b.take(na); p.B[k] = b.take(nb); }
     for (int k = 0; k < 3; ++k) { p.AP[k] = b.take(na); p.BP[k] = b.take(nb); }
     p.PA = b.take(nty * G.nz * ntx * kTX * partial_elem(o.acc));
-    p.PB = b.take(ntx * G.nz * (size_t)G.ny * partial_elem(o.acc));
+    p.PB = b.take(ntx * G.nz * align_up(G.ny, 4) * partial_elem(o.acc));
     p.PA2 = b.take(nty * G.nz * ntx * kTX * partial_elem(o.acc));
-    p.PB2 = b.take(ntx * G.nz * (size_t)G.ny * partial_elem(o.acc));
+    p.PB2 = b.take(ntx * G.nz * align_up(G.ny, 4) * partial_elem(o.acc));
     p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
   }
@@ -189,6 +189,39 @@ cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUte
   return cudaSuccess;
 }
 
+cudaError_t make_partial_maps(const GridDev& g, CUtensorMap tm[4], char* err, size_t errlen) {
+  auto enc = encode_fn();
+  if (!enc) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
+    return cudaErrorNotSupported;
+  }
+  // TwoSum partials are (hi, lo) float pairs: twice the FP32 elements per entry
+  const int per = g.acc == ABFT_ACC_TWOSUM ? 2 : 1;
+  const CUtensorMapDataType dt = g.acc == ABFT_ACC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const size_t esz = g.acc == ABFT_ACC_FP64 ? 8 : 4;
+  for (int k = 0; k < 4; ++k) {
+    const bool is_a = k < 2;
+    const size_t row = (size_t)(is_a ? g.pa_stride : g.pb_stride) * per;  // elements per (tile, plane) row
+    const int nt = is_a ? g.nty : g.ntx;
+    if (nt > 256) {  // box limit; the persistent kernel is not used for such grids
+      memset(&tm[k], 0, sizeof tm[k]);
+      continue;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)row, (cuuint64_t)g.nz, (cuuint64_t)nt};
+    cuuint64_t strides[2] = {(cuuint64_t)(row * esz), (cuuint64_t)(row * esz * g.nz)};
+    cuuint32_t box[3] = {(cuuint32_t)(kCheckBox * per), 1, (cuuint32_t)nt};
+    cuuint32_t ebox[3] = {1, 1, 1};
+    void* base = k == 0 ? g.PA : k == 1 ? g.PA2 : k == 2 ? g.PB : g.PB2;
+    CUresult r = enc(&tm[k], dt, 3, base, dims, strides, box, ebox, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      snprintf(err, errlen, "cuTensorMapEncodeTiled (partials) failed (%d)", (int)r);
+      return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
+}
+
 }  // namespace abft
 
 struct abft_ctx {
@@ -199,7 +232,7 @@ struct abft_ctx {
   std::vector<abft_grid> grids;
   std::vector<abft_coeffs> co;
   std::vector<GridDev> g;
-  std::vector<CUtensorMap> tm_u, tm_c;
+  std::vector<CUtensorMap> tm_u, tm_c, tm_p;
   std::vector<int> cur, ref;
   std::vector<int64_t> ref_step;
   std::vector<char> ck_valid;
@@ -403,7 +436,8 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
                        ctx->stream));
     int blocks = 0;
     CK(run(ctx, prot ? kKPersistProt : kKPersistPlain, [&] {
-      return launch_persistent(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], ctx->step, (int)n, c, p, q, prot, &blocks);
+      return launch_persistent(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], &ctx->tm_p[4 * gi], ctx->step, (int)n, c, p, q,
+                               prot, &blocks);
     }));
     ctx->cur[gi] = prot ? (int)((c + n) % 3) : (((n - 1) & 1) ? q : p);
     if (prot) {
@@ -713,6 +747,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.ntx = (G.nx + kTX - 1) / kTX;
     g.nty = (G.ny + g.ty - 1) / g.ty;
     g.pa_stride = g.ntx * kTX;
+    g.pb_stride = (int)align_up(G.ny, 4);
     g.acc = opt->acc;
     g.gid = i;
     g.eps = opt->eps;
@@ -738,6 +773,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   }
   ctx->tm_u.resize(3 * n_grids);
   ctx->tm_c.resize(n_grids);
+  ctx->tm_p.resize(4 * n_grids);
   ctx->cur.assign(n_grids, 0);
   ctx->ref.assign(n_grids, 0);
   ctx->ref_step.assign(n_grids, 0);
@@ -763,7 +799,8 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.C, g.cx, g.cy); }));
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[0], g.A[0], g.B[0]); }));
     char e[256];
-    if (make_tensor_maps(g, g.ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess) {
+    if (make_tensor_maps(g, g.ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess ||
+        make_partial_maps(g, &ctx->tm_p[4 * i], e, sizeof e) != cudaSuccess) {
       st = fail(ctx, ABFT_E_CUDA, "%s", e);
       return bail(st);
     }

@@ -66,6 +66,7 @@ struct GridDev {
   int nx, ny, nz, px;       // px: row pitch in elements (multiple of 32)
   int ntx, nty, ty;         // sweep tiles along x and y, rows per tile
   int pa_stride;            // row stride of the a-partials (ntx * kTX)
+  int pb_stride;            // row stride of the b-partials (ny rounded up to a multiple of 4)
   int acc;                  // abft_acc
   int shallow;              // 1: whole-column tiles (all nz planes staged at once)
   int gid;
@@ -89,6 +90,16 @@ struct DevFlip { long long step; int grid, z, y, x, bit, target; };
 struct DevSched {
   const DevFlip* flips;
   const int* off;           // off[i]..off[i+1]: flips of sweep sched_t0 + i (all grids)
+  // copies of the control block's injection fields, constant during a launch
+  int enabled;
+  int n;
+  long long t0;
+  // read them once, at the start of a kernel
+  __device__ __forceinline__ void load(const DevCtrl* c) {
+    enabled = c->inject_enabled;
+    t0 = c->sched_t0;
+    n = c->sched_n;
+  }
 };
 
 // host-side launchers (defined in sweep.cu / check.cu); all enqueue on `s`
@@ -101,6 +112,10 @@ struct Launch {
 
 cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUtensorMap* tm_c,
                              char* err, size_t errlen);
+// tensor maps of the partial buffers as seen by the persistent kernel's check warp:
+// [0] PA, [1] PA2, [2] PB, [3] PB2; boxes of 32 entries by all tiles of one plane
+cudaError_t make_partial_maps(const GridDev& g, CUtensorMap tm[4], char* err, size_t errlen);
+constexpr int kCheckBox = 32;  // entries per check-warp round
 int sweep_smem_bytes(int ty, bool prot);
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
                          const CUtensorMap& tm_c, int in, int out, bool prot);
@@ -113,7 +128,8 @@ cudaError_t launch_chain(const Launch& L, const GridDev& g, const double* a_in, 
 cudaError_t launch_compare(const Launch& L, const GridDev& g, const double* ap, const double* bp,
                            const double* a, const double* b);
 cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
-                              long long step0, int n_steps, int first_in, int p, int q, bool prot, int* blocks);
+                              const CUtensorMap tm_p[4], long long step0, int n_steps, int first_in, int p, int q,
+                              bool prot, int* blocks);
 bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);

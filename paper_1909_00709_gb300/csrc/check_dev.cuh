@@ -90,7 +90,7 @@ __device__ __forceinline__ double reduce_a(const GridDev& g, int z, int x, int p
 
 template <int ACC>
 __device__ __forceinline__ double reduce_b(const GridDev& g, int z, int y, int pbuf = 0) {
-  return sum_partials<ACC>(pbuf ? g.PB2 : g.PB, (size_t)z * g.ny + y, (size_t)g.nz * g.ny, g.ntx);
+  return sum_partials<ACC>(pbuf ? g.PB2 : g.PB, (size_t)z * g.pb_stride + y, (size_t)g.nz * g.pb_stride, g.ntx);
 }
 
 // Theorem 1 for the clamped 7-point set (Eq. 4 for a, Eq. 5 for b): shifts along the
@@ -378,8 +378,8 @@ struct CheckRound {
       const int b = e - na;
       const int z = b / g.ny, y = b - z * g.ny;
       *P = pbuf ? g.PB2 : g.PB;
-      *i0 = (size_t)z * g.ny + y;
-      *stride = (size_t)g.nz * g.ny;
+      *i0 = (size_t)z * g.pb_stride + y;
+      *stride = (size_t)g.nz * g.pb_stride;
       *n = g.ntx;
     }
   }

@@ -74,7 +74,7 @@ extern "C" ABFT_API abft_status abft_sweep_checksums_static(const float* u_in, c
 
   const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kStaticTy - 1) / kStaticTy;
   const size_t pa = round_up((size_t)nty * nz * ntx * kTX * sizeof(float), 256);
-  const size_t pb = round_up((size_t)ntx * nz * ny * sizeof(float), 256);
+  const size_t pb = round_up((size_t)ntx * nz * round_up(ny, 4) * sizeof(float), 256);
   if (kCtrlBytes + pa + pb > kScratchBytes) return ABFT_E_INVAL;  // grid too large for the array
 
   void* base = nullptr;
@@ -87,6 +87,7 @@ extern "C" ABFT_API abft_status abft_sweep_checksums_static(const float* u_in, c
   g.nx = nx; g.ny = ny; g.nz = nz; g.px = (int)pitch;
   g.ntx = ntx; g.nty = nty; g.ty = kStaticTy;
   g.pa_stride = ntx * kTX;
+  g.pb_stride = (int)round_up(ny, 4);
   g.acc = ABFT_ACC_FP32;
   g.gid = 0;
   g.eps = 1e-5;

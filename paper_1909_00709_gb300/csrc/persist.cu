@@ -24,6 +24,8 @@
 //   per sweep in the fault-free case instead of three.
 // Barrier waits are bounded: on timeout the status word is set and the launch winds
 // down instead of hanging.
+#include <algorithm>
+
 #include "check_dev.cuh"
 #include "sweep_tile.cuh"
 
@@ -32,6 +34,7 @@ namespace abft {
 struct PersistArgs {
   CUtensorMap tm_u[3];
   CUtensorMap tm_c;
+  CUtensorMap tm_p[4];  // partial buffers for the check warp: PA, PA2, PB, PB2
   GridDev g;
   long long step0;   // sweep index of the first sweep of this launch
   int n_steps;
@@ -42,9 +45,10 @@ struct PersistArgs {
 template <class Tiles>
 __global__ void __launch_bounds__(256, 2)
     k_persist_plain(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev,
-                    const DevSched sched) {
+                    DevSched sched) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const GridDev& g = a.g;
+  sched.load(ctrl);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
   if (threadIdx.x == 0) {
@@ -69,12 +73,116 @@ __global__ void __launch_bounds__(256, 2)
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
 }
 
+// ------------------------------------------------------------ check warp
+// The online kernel's check warp.  Entries are taken in rounds of 32 consecutive
+// entries of one plane (a[z][32 xb ...] or b[z][32 yb ...]); one TMA box brings all
+// tiles' partials of a round into shared memory (its own mbarrier), while each lane
+// loads its entry's interpolation inputs.  The lane then sums its entry's partials in
+// the canonical order (sum_partials) and tests as check_entry does, so the results
+// are bit-identical to the other paths.  Runs concurrently with the sweep warps and
+// takes no block-wide barrier.
+template <int ACC>
+__device__ __forceinline__ void check_warp_round(const PersistArgs& a, const GridDev& g, int in, int out, int pbuf,
+                                                 int round, unsigned char* buf, uint64_t* cbar, unsigned& phase,
+                                                 DevCtrl* ctrl, unsigned* any) {
+  using T = typename PartialType<ACC>::T;
+  constexpr int per = ACC == ABFT_ACC_TWOSUM ? 2 : 1;
+  const int lane = threadIdx.x & 31;
+  const int nxb = (g.nx + kCheckBox - 1) / kCheckBox;
+  const int ra = g.nz * nxb;
+  const bool is_a = round < ra;
+  int z, c, len, n;
+  const CUtensorMap* tm;
+  if (is_a) {
+    z = round / nxb;
+    c = (round - z * nxb) * kCheckBox;
+    len = g.nx; n = g.nty;
+    tm = &a.tm_p[pbuf];
+  } else {
+    const int nyb = (g.ny + kCheckBox - 1) / kCheckBox;
+    const int r = round - ra;
+    z = r / nyb;
+    c = (r - z * nyb) * kCheckBox;
+    len = g.ny; n = g.ntx;
+    tm = &a.tm_p[2 + pbuf];
+  }
+  if (lane == 0) {
+    fence_proxy_async();  // the previous round's reads of buf come before this TMA write
+    mbar_expect_tx(cbar, kCheckBox * per * (ACC == ABFT_ACC_FP64 ? 8 : 4) * n);
+    tma_load_3d(buf, tm, c * per, z, 0, cbar);
+  }
+  const int idx = c + lane;
+  const bool live = idx < len;
+  // interpolation inputs while the box is in flight
+  const int im = idx > 0 ? idx - 1 : 0, ip = idx < len - 1 ? idx + 1 : len - 1;
+  const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+  const double* V = is_a ? g.A[in] : g.B[in];
+  const double* CC = is_a ? g.cx : g.cy;
+  const Coef& k = g.k;
+  const bool asym = is_a ? k.cn != k.cs : k.cw != k.ce;
+  double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, cc = 0;
+  float ef = 0.f, el = 0.f;
+  if (live) {
+    v0 = __ldcg(V + (size_t)z * len + idx);
+    v1 = __ldcg(V + (size_t)z * len + im);
+    v2 = __ldcg(V + (size_t)z * len + ip);
+    v3 = __ldcg(V + (size_t)zm * len + idx);
+    v4 = __ldcg(V + (size_t)zp * len + idx);
+    cc = CC[(size_t)z * len + idx];
+    if (asym) {
+      const float* u = g.u[in];
+      if (is_a) {
+        const size_t pl = (size_t)z * g.ny * g.px;
+        ef = __ldcg(u + pl + idx);
+        el = __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + idx);
+      } else {
+        const size_t row = ((size_t)z * g.ny + idx) * g.px;
+        ef = __ldcg(u + row);
+        el = __ldcg(u + row + g.nx - 1);
+      }
+    }
+  }
+  mbar_wait(cbar, phase, ctrl);
+  phase ^= 1u;
+  const T* part = reinterpret_cast<const T*>(buf);
+  LaneSum t[kLanes];
+  if (live) {
+    int q = 0;
+    for (; q + kLanes <= n; q += kLanes) {
+#pragma unroll
+      for (int j = 0; j < kLanes; ++j) t[j].add(part[(q + j) * kCheckBox + lane]);
+    }
+#pragma unroll
+    for (int j = 0; j < kLanes; ++j)
+      if (q + j < n) t[j].add(part[(q + j) * kCheckBox + lane]);
+  }
+  __syncwarp();
+  if (!live) return;
+#pragma unroll
+  for (int j = 1; j < kLanes; ++j) t[0].merge<ACC>(t[j]);
+  const double s = t[0].total<ACC>();
+  double p;
+  if (is_a) {
+    const double edge = asym ? edge_term(k.cn, k.cs, ef, el) : 0.0;
+    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cn, k.cs), k.cw, k.ce, k.cb, k.ct, edge);
+    g.A[out][(size_t)z * len + idx] = s;
+    g.AP[0][(size_t)z * len + idx] = p;
+  } else {
+    const double edge = asym ? edge_term(k.cw, k.ce, ef, el) : 0.0;
+    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cw, k.ce), k.cn, k.cs, k.cb, k.ct, edge);
+    g.B[out][(size_t)z * len + idx] = s;
+    g.BP[0][(size_t)z * len + idx] = p;
+  }
+  if (fails(p, s, g.eps)) append_fail(g, z, is_a ? 0 : 1, idx, any);
+}
+
 // flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
 __device__ __forceinline__ float reapply_flips(float v, const GridDev& g, DevCtrl* ctrl, const DevSched& sched,
                                                long long step, int z, int y, int x) {
-  if (!ctrl->inject_enabled) return v;
-  const long long i = step - ctrl->sched_t0;
-  if (i < 0 || i >= ctrl->sched_n) return v;
+  (void)ctrl;
+  if (!sched.enabled) return v;
+  const long long i = step - sched.t0;
+  if (i < 0 || i >= sched.n) return v;
   for (int k = sched.off[i]; k < sched.off[i + 1]; ++k) {
     const DevFlip f = sched.flips[k];
     if (f.grid == g.gid && f.target == 0 && f.z == z && f.y == y && f.x == x)
@@ -150,14 +258,16 @@ __device__ void repair_next(const GridDev& g, const float* u_s, float* u_n, void
   __syncthreads();
 }
 
+constexpr int kOnlineThreads = kSweepThreads + 32;  // eight sweep warps and one check warp
+
 template <class Tiles, int TY, int ACC>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kOnlineThreads, 2)
     k_persist_online(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev,
-                     const DevSched sched) {
+                     DevSched sched) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ ResolveSmem rs;
-  __shared__ CheckShared csh;
   const GridDev& g = a.g;
+  sched.load(ctrl);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
   if (threadIdx.x == 0) {
@@ -167,51 +277,45 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   unsigned long long* bar = &g.gc->bar;
   const int ntiles = g.ntx * g.nty;
-  const int n_entries = g.nz * (g.nx + g.ny);
-  const int first_tile = blockIdx.x;
   const bool resident_c = (int)gridDim.x >= ntiles;
-  static_assert(256 == 32 * kLanes, "one warp per lane of the canonical sum");
+  const bool sweeper = threadIdx.x < kSweepThreads;
+  // the check warp's rounds and its shared-memory box (after the tiles' shared memory)
+  const int rounds = g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
+  const int r0 = (int)((long long)rounds * blockIdx.x / gridDim.x);
+  const int r1 = (int)((long long)rounds * (blockIdx.x + 1) / gridDim.x);
+  unsigned char* craw = smem_raw + Tiles::smem_bytes(g.nz);  // past the tiles' region
+  unsigned char* cbase = craw + ((128 - (smem_u32(craw) & 127)) & 127);
+  uint64_t* cbar = reinterpret_cast<uint64_t*>(cbase);
+  unsigned char* cbuf = cbase + 128;
+  unsigned cphase = 0;
+  if (threadIdx.x == kSweepThreads) {
+    mbar_init(cbar, 1);
+    fence_barrier_init();
+    for (int k = 0; k < 4; ++k) prefetch_tensormap(&a.tm_p[k]);
+  }
+  __syncthreads();
   bool ok = true;
   for (int k = 0; k <= a.n_steps && ok; ++k) {
     const long long s = a.step0 + k;
     const int cur = (a.first_in + k) % 3, nxt = (a.first_in + k + 1) % 3, prv = (a.first_in + k + 2) % 3;
     const int pb_cur = (int)(s & 1), pb_nxt = (int)((s + 1) & 1);
     const bool sweep = k < a.n_steps, check = k > 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[(s + 1) % 3] = 0;  // last read two sweeps ago
-    // a. loads of the first tile of this sweep
-    if (sweep && first_tile < ntiles)
-      tiles.issue(&a.tm_u[cur], &a.tm_c, g, first_tile % g.ntx, first_tile / g.ntx, s, ctrl, sched,
-                  !resident_c || k == 0);
-    // b. check u^s against the interpolation from a^{s-1}, b^{s-1}: this CTA's entries
-    //    [e0, e1) in rounds of 32; the first round's loads are issued now and consumed
-    //    after the sweep, so their latency hides under it
     unsigned* any = &g.gc->fails[s % 3];
-    const int e0 = (int)((long long)n_entries * blockIdx.x / gridDim.x);
-    const int e1 = (int)((long long)n_entries * (blockIdx.x + 1) / gridDim.x);
-    CheckRound<ACC> pre;
-    if (check) pre.load(g, prv, pb_cur, e0, e1);
-    // c. sweep u^s -> u^{s+1}
-    if (sweep) {
-      for (int tile = first_tile; tile < ntiles; tile += gridDim.x) {
-        if (tile != first_tile)
-          tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, true);
-        tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl, pb_nxt);
-      }
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[(s + 1) % 3] = 0;  // last read two sweeps ago
+    if (sweeper) {
+      // sweep warps: u^s -> u^{s+1}, partials into the other partial buffer
+      if (sweep)
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+          tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, !resident_c || k == 0);
+          tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl, pb_nxt);
+        }
+    } else if (check) {
+      // check warp, concurrently: u^s against the interpolation from a^{s-1}, b^{s-1}
+      for (int r = r0; r < r1; ++r) check_warp_round<ACC>(a, g, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, any);
     }
-    if (check) {
-      pre.finish(g, cur, pb_cur, any, csh);
-      for (int base = e0 + 32; base < e1; base += 64) {  // remaining rounds, two at a time
-        CheckRound<ACC> c0, c1;
-        c0.load(g, prv, pb_cur, base, e1);
-        c1.load(g, prv, pb_cur, base + 32, e1);
-        c0.finish(g, cur, pb_cur, any, csh);
-        c1.finish(g, cur, pb_cur, any, csh);
-      }
-    }
-    // d.
     ok = grid_barrier(bar, ctrl);
     if (!ok || !check) continue;
-    // e. rare: locate, correct, repair the speculative sweep
+    // rare: locate, correct, repair the speculative sweep
     if (ld_acquire_u32(any) != 0) {
       if (blockIdx.x == 0) {
         // u^s is the output of sweep s - 1; u^{s+1} that of sweep s
@@ -229,17 +333,25 @@ __global__ void __launch_bounds__(256, 2)
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
 }
 
+// extra dynamic shared memory of the online kernel's check warp: alignment slack,
+// mbarrier line, one box
+static int check_smem(const GridDev& g, int acc) {
+  const int per = acc == ABFT_ACC_TWOSUM ? 2 : 1, esz = acc == ABFT_ACC_FP64 ? 8 : 4;
+  return 256 + kCheckBox * per * esz * std::max(g.nty, g.ntx);
+}
+
 template <class Tiles, int TY, bool PROT, int ACC>
 static cudaError_t launch_persist_t(const Launch& L, const PersistArgs& a, int* blocks_out) {
   auto kern = PROT ? k_persist_online<Tiles, TY, ACC> : k_persist_plain<Tiles>;
-  const int smem = Tiles::smem_bytes(a.g.nz);
+  const int smem = Tiles::smem_bytes(a.g.nz) + (PROT ? check_smem(a.g, ACC) : 0);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  const int threads = PROT ? kOnlineThreads : 256;
   int per_sm = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -255,7 +367,7 @@ static cudaError_t launch_persist_t(const Launch& L, const PersistArgs& a, int* 
   abft_event* ev = L.events;
   DevSched sched = L.sched;
   void* args[] = {(void*)&a, (void*)&ctrl, (void*)&ev, (void*)&sched};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, smem, L.s);
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), args, smem, L.s);
 }
 
 template <class Tiles, int TY>
@@ -272,12 +384,15 @@ static cudaError_t launch_persist_ty(const Launch& L, const PersistArgs& a, bool
 // (the case it is built for; larger grids keep one launch per sweep).
 template <class Tiles, int TY>
 static bool fits_t(const GridDev& g, bool prot) {
+  if (prot && (g.nty > 256 || g.ntx > 256)) return false;  // one TMA box per check round
   const void* kern = prot ? (const void*)k_persist_online<Tiles, TY, ABFT_ACC_FP32> : (const void*)k_persist_plain<Tiles>;
-  const int smem = Tiles::smem_bytes(g.nz);
+  const int smem = Tiles::smem_bytes(g.nz) + (prot ? check_smem(g, g.acc) : 0);
+  if (smem > 227 * 1024) return false;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
   int per_sm = 0, sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, prot ? kOnlineThreads : 256, smem) != cudaSuccess)
+    return false;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
   return (long long)g.ntx * g.nty <= (long long)per_sm * sms;
 }
@@ -292,9 +407,11 @@ bool persistent_fits(const GridDev& g, bool prot) {
 }
 
 cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
-                              long long step0, int n_steps, int first_in, int p, int q, bool prot, int* blocks) {
+                              const CUtensorMap tm_p[4], long long step0, int n_steps, int first_in, int p, int q,
+                              bool prot, int* blocks) {
   PersistArgs a;
   for (int k = 0; k < 3; ++k) a.tm_u[k] = tm_u[k];
+  for (int k = 0; k < 4; ++k) a.tm_p[k] = tm_p[k];
   a.tm_c = tm_c;
   a.g = g;
   a.step0 = step0;

@@ -25,8 +25,9 @@ namespace abft {
 template <class Tiles, bool PROT, int ACC>
 __global__ void __launch_bounds__(256, 2)
     k_sweep(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c,
-            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, const DevSched sched) {
+            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  sched.load(ctrl);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
   if (threadIdx.x == 0) {

@@ -21,6 +21,12 @@
 
 namespace abft {
 
+// The tile code runs on the first kSweepThreads threads of a block and synchronises
+// them with named barrier 1, so that other warps of the block (the persistent online
+// kernel's check warp) can run independently.
+constexpr int kSweepThreads = 256;
+__device__ __forceinline__ void tile_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kSweepThreads) : "memory"); }
+
 template <int TY>
 struct SweepCfg {
   static constexpr int NW = 8;                        // warps per CTA
@@ -206,13 +212,13 @@ __device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const 
     }
     *sm.nlf = 0;
   }
-  __syncthreads();
+  tile_sync();
   // flips of this sweep that land in this tile (Sec. 5.1: after the update, before the store)
-  if (ctrl->inject_enabled) {
-    const long long i = step - ctrl->sched_t0;
-    if (i >= 0 && i < ctrl->sched_n) {
+  if (sched.enabled) {
+    const long long i = step - sched.t0;
+    if (i >= 0 && i < sched.n) {
       const int b = sched.off[i], e = sched.off[i + 1];
-      for (int k = b + tid; k < e; k += blockDim.x) {
+      for (int k = b + tid; k < e; k += kSweepThreads) {
         const DevFlip f = sched.flips[k];
         if (f.grid == g.gid && f.target == 0 && f.x >= x0 && f.x < x0 + kTX && f.x < g.nx && f.y >= y0 &&
             f.y < y0 + TY && f.y < g.ny && f.z >= 0 && f.z < nz && f.x >= 0 && f.y >= 0) {
@@ -223,7 +229,7 @@ __device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const 
       }
     }
   }
-  __syncthreads();
+  tile_sync();
 }
 
 template <int TY, bool PROT, int ACC>
@@ -316,12 +322,12 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
         float m[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
-        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.ny + y, yv && lane == 0);
+        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
         acc.add(m);
       }
     }
     if (PROT) acc.put(sm.red + (z & 1) * Cfg::RED_HALF, warp, lane);
-    __syncthreads();
+    tile_sync();
     if (tid == 0 && z >= 1 && z - 1 + S < nz) {
       fence_proxy_async();
       issue(z - 1 + S);
@@ -332,7 +338,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
   }
   seq = base + (unsigned)nz;
   fence_proxy_async_global();  // this thread's grid stores, before any later TMA read of them
-  __syncthreads();             // the ring and the reduction buffer are idle again
+  tile_sync();             // the ring and the reduction buffer are idle again
 }
 
 template <int TY, bool PROT, int ACC>
@@ -400,7 +406,7 @@ __device__ void recompute_pb(const GridDev& g, const float* __restrict__ u, void
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     m[i] = (y < g.ny && gx0 + i < g.nx) ? __ldcg(u + ((size_t)z * g.ny + y) * g.px + gx0 + i) : 0.f;
-  AccA<ACC>::row_store(m, PB, ((size_t)txi * g.nz + z) * g.ny + y, lane == 0);
+  AccA<ACC>::row_store(m, PB, ((size_t)txi * g.nz + z) * g.pb_stride + y, lane == 0);
 }
 
 // --------------------------------------------- multi-row reduction of row partials
@@ -536,12 +542,12 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
     if (load_c) tma_load_3d(sm.c, tm_c, x0, y0, 0, sm.bar);
     *sm.nlf = 0;
   }
-  __syncthreads();
-  if (ctrl->inject_enabled) {
-    const long long i = step - ctrl->sched_t0;
-    if (i >= 0 && i < ctrl->sched_n) {
+  tile_sync();
+  if (sched.enabled) {
+    const long long i = step - sched.t0;
+    if (i >= 0 && i < sched.n) {
       const int b = sched.off[i], e = sched.off[i + 1];
-      for (int k = b + tid; k < e; k += blockDim.x) {
+      for (int k = b + tid; k < e; k += kSweepThreads) {
         const DevFlip f = sched.flips[k];
         if (f.grid == g.gid && f.target == 0 && f.x >= x0 && f.x < x0 + kTX && f.x < g.nx && f.y >= y0 &&
             f.y < y0 + TY && f.y < g.ny && f.z >= 0 && f.z < nz && f.x >= 0 && f.y >= 0) {
@@ -552,7 +558,7 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
       }
     }
   }
-  __syncthreads();
+  tile_sync();
 }
 
 template <int TY, bool PROT, int ACC>
@@ -641,11 +647,11 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
       const typename RowPart<ACC>::T tot = reduce_rows<ACC, TY>(rp, lane);
       constexpr int SH = TY == 8 ? 2 : 1;  // lane l holds row l >> SH
       const int r = lane >> SH, y = y0 + r;
-      if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny) RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.ny + y, tot);
+      if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny) RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.pb_stride + y, tot);
     }
   }
   fence_proxy_async_global();
-  __syncthreads();
+  tile_sync();
 }
 
 // a-partial of column x of shallow tile tyi in plane z, in the shallow tile's order
@@ -680,7 +686,7 @@ struct StreamTiles {
   static constexpr int NW = SweepCfg<TY>::NW;
   SweepSmem<TY> sm;
   unsigned seq;
-  __host__ static int smem_bytes(int) { return SweepCfg<TY>::SMEM; }
+  __host__ __device__ static int smem_bytes(int) { return SweepCfg<TY>::SMEM; }
   __device__ __forceinline__ void setup(unsigned char* raw, int) {
     sm = SweepSmem<TY>::carve(raw);
     seq = 0;
@@ -706,7 +712,7 @@ struct ShallowTiles {
   static constexpr int NW = ShallowCfg<TY>::NW;
   ShallowSmem<TY> sm;
   unsigned phase;
-  __host__ static int smem_bytes(int nz) { return ShallowCfg<TY>::smem(nz); }
+  __host__ __device__ static int smem_bytes(int nz) { return ShallowCfg<TY>::smem(nz); }
   __device__ __forceinline__ void setup(unsigned char* raw, int nz) {
     sm = ShallowSmem<TY>::carve(raw, nz);
     phase = 0;
