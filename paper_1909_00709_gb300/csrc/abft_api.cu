@@ -452,6 +452,37 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
   return ABFT_OK;
 }
 
+// `n` sweeps of every grid in offline windows, one persistent launch per grid
+abft_status persistent_offline_all(abft_ctx* ctx, int64_t n) {
+  const Launch L = launcher(ctx);
+  const int delta = std::max(ctx->opt.delta, 1);
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    abft_status s = ensure_checksums(ctx, gi);
+    if (s) return s;
+    const GridDev& g = ctx->g[gi];
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned) + sizeof(unsigned long long),
+                       ctx->stream));
+    int blocks = 0;
+    const int ck = ctx->cur[gi];
+    CK(run(ctx, kKPersistProt, [&] {
+      return launch_persistent_offline(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], ctx->step, (int)n, delta, ck, &blocks);
+    }));
+    // the buffer roles follow the window lengths only (a recomputed window reuses its buffers)
+    int c = ck;
+    for (int64_t t = 0; t < n; t += delta) {
+      const int64_t d = std::min<int64_t>(delta, n - t);
+      const int w0 = (c + 1) % 3, w1 = (c + 2) % 3;
+      c = ((d - 1) & 1) ? w1 : w0;
+    }
+    ctx->cur[gi] = c;
+    ctx->ref[gi] = c;
+    ctx->ref_step[gi] = ctx->step + n;
+    ctx->ck_valid[gi] = 1;
+  }
+  ctx->step += n;
+  return ABFT_OK;
+}
+
 // one sweep of every grid; protected sweeps write partial checksums
 abft_status sweep_all(abft_ctx* ctx, int mode) {
   const Launch L = launcher(ctx);
@@ -482,6 +513,8 @@ abft_status status_from_device(abft_ctx* ctx) {
   ctx->status_seen |= st;
   if (st & kStTimeout) return fail(ctx, ABFT_E_TIMEOUT, "a device-side wait timed out");
   if (st & kStFlipOverflow) return fail(ctx, ABFT_E_INVAL, "more than %d flips in one tile and sweep", kLocalFlips);
+  if (st & kStUncorrectable)
+    return fail(ctx, ABFT_E_UNCORRECTABLE, "an offline window still mismatched after its recomputation");
   if (st & kStEventOverflow) return fail(ctx, ABFT_E_TRUNCATED, "event log overflow (capacity %d)", ctx->opt.event_capacity);
   return ABFT_OK;
 }
@@ -857,12 +890,28 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
   abft_status s = ABFT_OK;
   while (ctx->step < t_end) {
     int64_t want = std::min<int64_t>(t_end - ctx->step, kSchedSteps);
-    if (mode == ABFT_MODE_OFFLINE) want = std::min<int64_t>(want, std::max<int64_t>(ctx->opt.delta, 1));
+    bool persist_off = false;
+    if (mode == ABFT_MODE_OFFLINE) {
+      const int64_t delta = std::max<int64_t>(ctx->opt.delta, 1);
+      persist_off = ctx->opt.persistent != 0;
+      for (int gi = 0; gi < ctx->n && persist_off; ++gi) persist_off = persistent_offline_fits(ctx->g[gi]);
+      if (persist_off) {
+        if (want > delta && want < t_end - ctx->step) want -= want % delta;  // whole windows per launch
+      } else {
+        want = std::min<int64_t>(want, delta);
+      }
+    }
     int64_t covered = 0;
     s = upload_schedule(ctx, ctx->step, want, &covered);
     if (s) return s;
     if (mode == ABFT_MODE_OFFLINE) {
-      s = offline_window(ctx, covered);
+      if (persist_off) {
+        const int64_t delta = std::max<int64_t>(ctx->opt.delta, 1);
+        if (covered > delta && covered < t_end - ctx->step) covered -= covered % delta;
+        s = persistent_offline_all(ctx, covered);
+      } else {
+        s = offline_window(ctx, covered);
+      }
       if (s) return s;
       continue;
     }
@@ -1005,7 +1054,9 @@ abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out) {
   out->steps_done = ctx->step;
   out->kernel_launches = ctx->launches;
   out->events = (int64_t)ctx->h_ctrl->ev_count;
-  out->rollbacks = ctx->rollbacks;
+  int64_t dev_rollbacks = 0;
+  for (int gi = 0; gi < ctx->n; ++gi) dev_rollbacks += ctx->h_gctrl[gi].rollbacks;
+  out->rollbacks = ctx->rollbacks + dev_rollbacks;
   out->flips_scheduled = ctx->flips_scheduled;
   return ABFT_OK;
 }

@@ -25,7 +25,8 @@ enum : unsigned {
   kStTimeout = 1u,        // a TMA/mbarrier wait gave up
   kStFlipOverflow = 2u,   // more flips in one tile and sweep than kLocalFlips
   kStEventOverflow = 4u,  // event log full
-  kStFailOverflow = 8u    // more failing entries in a plane than kFCap (plane recomputed)
+  kStFailOverflow = 8u,   // more failing entries in a plane than kFCap (plane recomputed)
+  kStUncorrectable = 16u  // an offline window still mismatched after its recomputation
 };
 
 // kernel kinds for launch accounting and abft_time_kernels
@@ -53,7 +54,7 @@ struct DevGridCtrl {
   unsigned int done_sweep;  // last-block tickets
   unsigned int done_check;
   unsigned int done_aux;
-  unsigned int pad;
+  unsigned int rollbacks;   // offline windows the persistent kernel recomputed
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
   unsigned int pad2;
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
@@ -130,6 +131,11 @@ cudaError_t launch_compare(const Launch& L, const GridDev& g, const double* ap, 
 cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
                               const CUtensorMap tm_p[4], long long step0, int n_steps, int first_in, int p, int q,
                               bool prot, int* blocks);
+// offline windows of `delta` sweeps from checkpoint buffer `ck` (Sec. 4), in one launch
+cudaError_t launch_persistent_offline(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3],
+                                      const CUtensorMap& tm_c, long long step0, int n_steps, int delta, int ck,
+                                      int* blocks);
+bool persistent_offline_fits(const GridDev& g);
 bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);

@@ -25,6 +25,7 @@
 // Barrier waits are bounded: on timeout the status word is set and the launch winds
 // down instead of hanging.
 #include <algorithm>
+#include <cstring>
 
 #include "check_dev.cuh"
 #include "sweep_tile.cuh"
@@ -38,8 +39,9 @@ struct PersistArgs {
   GridDev g;
   long long step0;   // sweep index of the first sweep of this launch
   int n_steps;
-  int first_in;      // buffer of the first sweep's input
+  int first_in;      // buffer of the first sweep's input (offline: the checkpoint)
   int p, q;          // then outputs alternate p, q, p, ... (sweep k >= 1 reads the previous output)
+  int delta;         // offline detection period
 };
 
 template <class Tiles>
@@ -340,6 +342,162 @@ static int check_smem(const GridDev& g, int acc) {
   return 256 + kCheckBox * per * esz * std::max(g.nty, g.ntx);
 }
 
+// ---------------------------------------------------------------- offline
+// Windows of d = delta sweeps (the last may be shorter) from a checkpoint ck (Sec. 4):
+//   sweeps ck -> W0 -> W1 -> W0 ... (the last one protected, writing partials), while the
+//   spare warp advances the chain of Fig. 10 one link per sweep: P^0 = a(ck),
+//   P^{k+1} = Theorem 1 applied to P^k (boundary terms vanish), into AP[(k+1) & 1];
+//   after the window every thread reduces a slice of the partials into a(F) and compares
+//   with P^d; on a mismatch the window is recomputed from ck without injection (the same
+//   buffers, so the roles stay fixed) and compared again.  Then F becomes the checkpoint.
+// One grid barrier per sweep plus one per window.
+__device__ __forceinline__ void window_buffers(int ck, int& w0, int& w1) {
+  w0 = (ck + 1) % 3;
+  w1 = (ck + 2) % 3;
+}
+
+template <class Tiles, int TY, int ACC>
+__global__ void __launch_bounds__(kOnlineThreads, 2)
+    k_persist_offline(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl,
+                      abft_event* __restrict__ ev, DevSched sched) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const GridDev& g = a.g;
+  sched.load(ctrl);
+  Tiles tiles;
+  tiles.setup(smem_raw, g.nz);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) prefetch_tensormap(&a.tm_u[k]);
+    prefetch_tensormap(&a.tm_c);
+  }
+  __syncthreads();
+  unsigned long long* bar = &g.gc->bar;
+  const int ntiles = g.ntx * g.nty;
+  const bool resident_c = (int)gridDim.x >= ntiles;
+  const bool sweeper = threadIdx.x < kSweepThreads;
+  const int na = g.nz * g.nx, n_entries = g.nz * (g.nx + g.ny);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gsize = (long long)gridDim.x * blockDim.x;
+  const int c0 = (int)((long long)n_entries * blockIdx.x / gridDim.x);  // chain slice of this CTA
+  const int c1 = (int)((long long)n_entries * (blockIdx.x + 1) / gridDim.x);
+  int ck = a.first_in;
+  bool ok = true, first_load = true;
+  long long t = a.step0;
+  const long long t_end = a.step0 + a.n_steps;
+  while (t < t_end && ok) {
+    const int d = (int)min((long long)a.delta, t_end - t);
+    int w[2];
+    window_buffers(ck, w[0], w[1]);
+    const int fin = w[(d - 1) & 1];
+    for (int attempt = 0; attempt < 2 && ok; ++attempt) {
+      DevSched sw = sched;
+      if (attempt) sw.enabled = 0;  // a recomputed window is fault-free
+      for (int k = 0; k < d && ok; ++k) {
+        const int in = k == 0 ? ck : w[(k - 1) & 1], out = w[k & 1];
+        const long long s = t + k;
+        if (sweeper) {
+          for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            tiles.issue(&a.tm_u[in], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sw, !resident_c || first_load);
+            if (k == d - 1)
+              tiles.template run<true, ACC>(&a.tm_u[in], &a.tm_c, g, g.u[out], tile % g.ntx, tile / g.ntx, ctrl, 0);
+            else
+              tiles.template run<false, ACC>(&a.tm_u[in], &a.tm_c, g, g.u[out], tile % g.ntx, tile / g.ntx, ctrl, 0);
+          }
+        } else if (attempt == 0) {
+          // one link of the chain, this CTA's slice, concurrently with the sweep
+          const double* pa = k == 0 ? g.A[ck] : g.AP[k & 1];
+          const double* pb = k == 0 ? g.B[ck] : g.BP[k & 1];
+          double* qa = g.AP[(k + 1) & 1];
+          double* qb = g.BP[(k + 1) & 1];
+          for (int e = c0 + (int)(threadIdx.x & 31); e < c1; e += 32) {
+            if (e < na) {
+              const int z = e / g.nx, x = e - z * g.nx;
+              qa[e] = predict_a(g, pa, nullptr, z, x);
+            } else {
+              const int b = e - na, z = b / g.ny, y = b - z * g.ny;
+              qb[b] = predict_b(g, pb, nullptr, z, y);
+            }
+          }
+        }
+        first_load = false;
+        ok = grid_barrier(bar, ctrl);
+      }
+      if (!ok) break;
+      // compare the recomputed checksums of the window's result with the chain
+      if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[attempt] = 0;
+      ok = grid_barrier(bar, ctrl);
+      if (!ok) break;
+      const double* pa = g.AP[d & 1];
+      const double* pb = g.BP[d & 1];
+      unsigned nf = 0;
+      for (long long i = gtid; i < n_entries; i += gsize) {
+        if (i < na) {
+          const int z = (int)i / g.nx, x = (int)i - z * g.nx;
+          const double sum = reduce_a<ACC>(g, z, x, 0);
+          g.A[fin][i] = sum;
+          nf += fails(__ldcg(pa + i), sum, g.eps) ? 1u : 0u;
+        } else {
+          const int b = (int)(i - na), z = b / g.ny, y = b - z * g.ny;
+          const double sum = reduce_b<ACC>(g, z, y, 0);
+          g.B[fin][b] = sum;
+          nf += fails(__ldcg(pb + b), sum, g.eps) ? 1u : 0u;
+        }
+      }
+      if (nf) atomicAdd(&g.gc->fails[attempt], nf);
+      ok = grid_barrier(bar, ctrl);
+      if (!ok) break;
+      const unsigned bad = ld_acquire_u32(&g.gc->fails[attempt]);
+      if (bad == 0) break;
+      if (attempt == 1) {  // the fault-free recomputation must verify
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctrl, kStUncorrectable);
+        ok = false;
+        break;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {  // Sec. 4.2: restore the checkpoint and recompute
+        log_event(ctrl, ev, t, g.gid, -1, -1, -1, ABFT_EV_ROLLBACK, (float)bad, (float)d);
+        atomicAdd(&g.gc->rollbacks, 1u);
+      }
+    }
+    ck = fin;
+    t += d;
+  }
+  if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = t_end;
+}
+
+template <class Tiles, int TY, int ACC>
+static cudaError_t launch_offline_t(const Launch& L, const PersistArgs& a, int* blocks_out) {
+  auto kern = k_persist_offline<Tiles, TY, ACC>;
+  const int smem = Tiles::smem_bytes(a.g.nz);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOnlineThreads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int ntiles = a.g.ntx * a.g.nty;
+  int blocks = std::min(per_sm * sms, ntiles);
+  if (blocks < 1) return cudaErrorInvalidConfiguration;
+  const int rounds = (ntiles + blocks - 1) / blocks;
+  blocks = (ntiles + rounds - 1) / rounds;
+  *blocks_out = blocks;
+  DevCtrl* ctrl = L.ctrl;
+  abft_event* ev = L.events;
+  DevSched sched = L.sched;
+  void* args[] = {(void*)&a, (void*)&ctrl, (void*)&ev, (void*)&sched};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kOnlineThreads), args, smem, L.s);
+}
+
+template <class Tiles, int TY>
+static cudaError_t launch_offline_ty(const Launch& L, const PersistArgs& a, int* blocks) {
+  switch (a.g.acc) {
+    case ABFT_ACC_TWOSUM: return launch_offline_t<Tiles, TY, ABFT_ACC_TWOSUM>(L, a, blocks);
+    case ABFT_ACC_FP64: return launch_offline_t<Tiles, TY, ABFT_ACC_FP64>(L, a, blocks);
+    default: return launch_offline_t<Tiles, TY, ABFT_ACC_FP32>(L, a, blocks);
+  }
+}
+
 template <class Tiles, int TY, bool PROT, int ACC>
 static cudaError_t launch_persist_t(const Launch& L, const PersistArgs& a, int* blocks_out) {
   auto kern = PROT ? k_persist_online<Tiles, TY, ACC> : k_persist_plain<Tiles>;
@@ -431,6 +589,54 @@ cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorM
     case 16: return launch_persist_ty<StreamTiles<16>, 16>(L, a, prot, blocks);
     case 32: return launch_persist_ty<StreamTiles<32>, 32>(L, a, prot, blocks);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_persistent_offline(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3],
+                                      const CUtensorMap& tm_c, long long step0, int n_steps, int delta, int ck,
+                                      int* blocks) {
+  PersistArgs a;
+  memset(&a, 0, sizeof a);
+  for (int k = 0; k < 3; ++k) a.tm_u[k] = tm_u[k];
+  a.tm_c = tm_c;
+  a.g = g;
+  a.step0 = step0;
+  a.n_steps = n_steps;
+  a.first_in = ck;
+  a.delta = delta;
+  if (g.shallow) {
+    switch (g.ty) {
+      case 8: return launch_offline_ty<ShallowTiles<8>, 8>(L, a, blocks);
+      case 16: return launch_offline_ty<ShallowTiles<16>, 16>(L, a, blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (g.ty) {
+    case 8: return launch_offline_ty<StreamTiles<8>, 8>(L, a, blocks);
+    case 16: return launch_offline_ty<StreamTiles<16>, 16>(L, a, blocks);
+    case 32: return launch_offline_ty<StreamTiles<32>, 32>(L, a, blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Tiles, int TY>
+static bool offline_fits_t(const GridDev& g) {
+  const void* kern = (const void*)k_persist_offline<Tiles, TY, ABFT_ACC_FP32>;
+  const int smem = Tiles::smem_bytes(g.nz);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+  int per_sm = 0, sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOnlineThreads, smem) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  return (long long)g.ntx * g.nty <= (long long)per_sm * sms;
+}
+
+bool persistent_offline_fits(const GridDev& g) {
+  if (g.shallow) return g.ty == 8 ? offline_fits_t<ShallowTiles<8>, 8>(g) : offline_fits_t<ShallowTiles<16>, 16>(g);
+  switch (g.ty) {
+    case 8: return offline_fits_t<StreamTiles<8>, 8>(g);
+    case 16: return offline_fits_t<StreamTiles<16>, 16>(g);
+    default: return offline_fits_t<StreamTiles<32>, 32>(g);
   }
 }
 

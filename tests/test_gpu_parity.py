@@ -110,11 +110,13 @@ def test_online_multi_flip_patterns(abi, orc, case, persistent):
     assert rel_err(got, ref["u"]) < value_tol(steps)
 
 
-@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5)])
-def test_offline_rollback_parity(abi, orc, shape):
+@pytest.mark.parametrize("shallow", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("shape", [(64, 64, 8), (200, 37, 5), (140, 70, 19)])
+def test_offline_rollback_parity(abi, orc, shape, persistent, shallow):
     steps = 40
     flips = inputs.flip_list([(20, 0, 2, 10, 11, 28), (35, 0, 1, 3, 4, 30), (9, 0, 0, 1, 2, 3)])
-    with gpu_context(abi, [shape], [4]) as ctx:
+    with gpu_context(abi, [shape], [4], persistent=persistent, shallow=shallow) as ctx:
         ctx.inject_list(flips)
         ctx.step(steps, OFFLINE)
         got = ctx.read(0)
@@ -197,13 +199,31 @@ def test_mixed_modes_continue_consistently(abi, orc):
     assert rel_err(got, ref["u"]) < 1e-5
 
 
-def test_offline_fault_free_equals_unprotected(abi):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_offline_fault_free_equals_unprotected(abi, persistent):
     shape = (129, 17, 3)
-    with gpu_context(abi, [shape], [6]) as a, gpu_context(abi, [shape], [6]) as b:
+    with gpu_context(abi, [shape], [6], persistent=persistent) as a, gpu_context(abi, [shape], [6]) as b:
         a.step(37, OFFLINE)
         b.step(37, NONE)
         assert len(a.events()) == 0
         np.testing.assert_array_equal(a.read(0), b.read(0))
+
+
+@pytest.mark.parametrize("delta", [1, 5, 16])
+def test_offline_persistent_and_per_launch_agree_bitwise(abi, delta):
+    shape, steps = (300, 130, 6), 45
+    flips = inputs.flip_list([(3, 0, 2, 5, 7, 30), (11, 0, 4, 60, 100, 22), (12, 0, 1, 3, 3, 9),
+                              (33, 0, 5, 129, 299, 31), (44, 0, 0, 0, 0, 26)])
+    out = []
+    for persistent in (0, 1):
+        with gpu_context(abi, [shape], [15], persistent=persistent, delta=delta) as ctx:
+            ctx.inject_list(flips)
+            ctx.step(20, OFFLINE)
+            ctx.step(steps - 20, OFFLINE)
+            ev = ctx.events()
+            out.append((ctx.read(0), sorted(map(tuple, ev[["step", "kind"]].tolist())), ctx.counters()["rollbacks"]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2] >= 1
 
 
 def test_two_grids_in_one_context(abi, orc):
