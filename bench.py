@@ -37,6 +37,11 @@ SWEEPS = 1000
 RATE = 1e-3
 BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
+PRECISION_SHAPE = (512, 512, 64)
+PRECISION_SWEEPS = 500
+LARGE_SHAPE = (1024, 1024, 256)
+LARGE_SWEEPS = 200
+ACC_NAMES = ("fp32", "twosum", "fp64")
 
 
 def parse():
@@ -47,6 +52,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-side", action="store_true", help="skip the precision study and the large grid")
     p.add_argument("--profile", action="store_true",
                    help="short run for profilers: warm-up jobs, then one protected and one plain job")
     p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
@@ -212,6 +218,7 @@ def run_ours(args, rank, world, local):
     ms_off = timed_jobs(off, abi.MODE_OFFLINE, args.steps)
     events = prot.events()
     off_cnt = off.counters()
+    side = side_runs(dev, stream, flush) if (rank == 0 and not args.no_side) else None
 
     # dominant kernel: average launch duration from CUDA events on the launching stream.
     # A persistent launch runs many sweeps; its algorithmic bytes are 12 B per point and sweep.
@@ -288,9 +295,74 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if side:
+        line.update(side)
+        line["large"]["roofline_frac"] = {k: v * BYTES_PER_UPDATE / peak for k, v in side["large"]["glups"].items()}
     print(json.dumps(line), flush=True)
     for c in (prot, plain, off):
         c.close()
+
+
+def side_runs(dev, stream, flush):
+    """The precision study (fault-free 512x512x64, three checksum accumulations) and the
+    large 1024x1024x256 grid (unprotected / online / offline), each timed with CUDA events."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1909_00709_gb300 import abi, inputs
+
+    def timed(shape, mode, sweeps, seed, inject=0.0, **opt):
+        t, p = inputs.grid_inputs(*shape, seed=seed)
+        with abi.Context([shape], [t], [p], [inputs.hotspot_coeffs(*shape)], device=dev, stream=stream,
+                         **opt) as c:
+            if inject:
+                c.inject(seed, inject, 0xFFFFFFFF)
+            c.step(3, mode)
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(sweeps, mode)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            n = shape[0] * shape[1] * shape[2]
+            return n * sweeps / (ms / 1e3) / 1e9, c
+
+    prec = {}
+    shape = PRECISION_SHAPE
+    for acc, name in enumerate(ACC_NAMES):
+        glups, _ = timed(shape, abi.MODE_ONLINE, PRECISION_SWEEPS, 2, acc=acc)
+        t, p = inputs.grid_inputs(*shape, seed=2)
+        with abi.Context([shape], [t], [p], [inputs.hotspot_coeffs(*shape)], device=dev, stream=stream,
+                         acc=acc, track_residual=1) as c:
+            c.step(PRECISION_SWEEPS, abi.MODE_ONLINE)
+            r = c.counters()["max_residual"]
+            n_ev = len(c.events())
+            u = c.read(0).astype(np.float64)
+            a, b = c.read_checksums(0)
+        a_ex, b_ex = u.sum(axis=1), u.sum(axis=2)  # FP64 sums of the FP32 grid
+        err = max(float(np.max(np.abs(a - a_ex) / np.abs(a_ex))), float(np.max(np.abs(b - b_ex) / np.abs(b_ex))))
+        eps = 4.0 * r
+        # smallest mantissa bit whose flip moves every checksum it enters by more than the
+        # calibrated threshold plus the residual: |delta| = 2^(bit - 23 + e), e the value's binade
+        e_min = math.floor(math.log2(float(u.min())))
+        top = max(float(a_ex.max()), float(b_ex.max()))
+        bit = max(0, math.ceil(math.log2(1.25 * eps * top) - e_min + 23))
+        prec[name] = {"glups": glups, "max_residual": r, "false_positives": n_ev, "checksum_rel_err": err,
+                      "eps_calibrated": eps, "detectable_bit": bit}
+    large = {}
+    lam = 1e-6 * math.prod(LARGE_SHAPE)  # flips per sweep
+    for name, mode, rate in (("unprotected", abi.MODE_NONE, 0.0), ("online", abi.MODE_ONLINE, 0.0),
+                             ("offline", abi.MODE_OFFLINE, 0.0), ("online_flips", abi.MODE_ONLINE, lam),
+                             ("offline_flips", abi.MODE_OFFLINE, lam)):
+        large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511)
+    return {"precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
+                          "variants": prec},
+            "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,
+                      "flip_rate_per_sweep": "1e-6 per point in the *_flips runs", "glups": large,
+                      "overhead_pct": {k: (large["unprotected"] / v - 1.0) * 100.0
+                                       for k, v in large.items() if k != "unprotected"}}}
 
 
 def run_profile(args, local):

@@ -96,6 +96,8 @@ typedef struct {
                                launch per grid and schedule chunk; 0: one launch per kernel */
   int32_t shallow;          /* 1: grids with nz <= 16 use whole-column tiles (all planes staged
                                at once); 0: always stream the planes */
+  int32_t track_residual;   /* 1: keep the largest relative residual |a'-a|/|a| of the entries
+                               that pass (abft_counters.max_residual); costs one atomic per entry */
   void* stream;             /* cudaStream_t used for all device work */
 } abft_options;
 
@@ -117,6 +119,7 @@ typedef struct {
   int64_t events;           /* events recorded (may exceed event_capacity) */
   int64_t rollbacks;        /* offline windows recomputed */
   int64_t flips_scheduled;  /* flips handed to the device */
+  double max_residual;      /* largest passing |a'-a|/|a| so far (0 unless track_residual) */
 } abft_counters;
 
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
@@ -186,6 +189,11 @@ ABFT_API abft_status abft_events(abft_ctx* ctx, abft_event* buf, int64_t cap, in
 /* Copy grid g's current state (nx*ny*nz FP32, unpadded) to dst (host or device). */
 ABFT_API abft_status abft_read(abft_ctx* ctx, int32_t grid, float* dst);
 
+/* Copy grid g's checksum vectors of the current state, a (nz*nx) and b (nz*ny), FP64,
+   to host or device memory (Eq. 2, 3; computed first if the last sweeps were
+   unprotected). */
+ABFT_API abft_status abft_read_checksums(abft_ctx* ctx, int32_t grid, double* a, double* b);
+
 /* Device pointer and row pitch (elements) of grid g's current state, valid until
    the next abft_step/abft_correct. */
 ABFT_API abft_status abft_current(abft_ctx* ctx, int32_t grid, float** dev_ptr, int64_t* pitch);
@@ -202,6 +210,19 @@ ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, d
 
 ABFT_API const char* abft_last_error(const abft_ctx* ctx);
 ABFT_API const char* abft_status_string(abft_status s);
+
+/* Self-test of failure detection without a fault: make one bounded device wait run out
+   on purpose and report how it ended.
+     which 0: a grid barrier (the one the persistent kernels use) that the last CTA of a
+              4-CTA launch never reaches;
+     which 1: an mbarrier wait (the one every TMA copy uses) for 16 bytes of transaction
+              that no copy delivers.
+   limit_us (1 ms .. 10 s) bounds the wait. Returns ABFT_E_TIMEOUT when the kernel gave
+   up, set its timeout status and returned (the expected outcome), ABFT_OK if the wait
+   ended some other way, ABFT_E_INVAL for bad arguments, ABFT_E_CUDA on a runtime
+   error. *elapsed_ms receives the kernel's duration (CUDA events on `stream`). Uses a
+   file-scope device control block: serialise calls; allocates nothing. */
+ABFT_API abft_status abft_selftest_wait(int32_t which, int64_t limit_us, void* stream, double* elapsed_ms);
 
 /* One protected sweep (Eq. 1 with the fused checksum epilogue) and the per-plane
    checksums a[z][x], b[z][y] of its result, for callers that cannot allocate

@@ -26,7 +26,8 @@ STATUS = {0: "ABFT_OK", 1: "ABFT_E_INVAL", 2: "ABFT_E_CUDA", 3: "ABFT_E_NOMEM", 
 EXPORTS = ("abft_default_options", "abft_workspace_bytes", "abft_init", "abft_step", "abft_verify",
            "abft_correct", "abft_inject", "abft_inject_list", "abft_schedule", "abft_events",
            "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
-           "abft_last_error", "abft_status_string", "abft_destroy", "abft_sweep_checksums_static")
+           "abft_last_error", "abft_status_string", "abft_destroy", "abft_sweep_checksums_static",
+           "abft_read_checksums", "abft_selftest_wait")
 
 
 class abft_grid(ct.Structure):
@@ -41,12 +42,12 @@ class abft_options(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
-                ("stream", ct.c_void_p)]
+                ("track_residual", ct.c_int32), ("stream", ct.c_void_p)]
 
 
 class abft_counters(ct.Structure):
     _fields_ = [("steps_done", ct.c_int64), ("kernel_launches", ct.c_int64), ("events", ct.c_int64),
-                ("rollbacks", ct.c_int64), ("flips_scheduled", ct.c_int64)]
+                ("rollbacks", ct.c_int64), ("flips_scheduled", ct.c_int64), ("max_residual", ct.c_double)]
 
 
 class abft_event(ct.Structure):
@@ -103,6 +104,8 @@ def lib(build_if_missing: bool = False):
     L.abft_events.argtypes = [P, P, I64, ct.POINTER(I64)]
     L.abft_read.argtypes = [P, I32, P]
     L.abft_current.argtypes = [P, I32, ct.POINTER(P), ct.POINTER(I64)]
+    L.abft_read_checksums.argtypes = [P, I32, P, P]
+    L.abft_selftest_wait.argtypes = [I32, I64, P, ct.POINTER(ct.c_double)]
     L.abft_get_counters.argtypes = [P, ct.POINTER(abft_counters)]
     L.abft_time_kernels.argtypes = [P, I64, I32, P, P]
     L.abft_last_error.argtypes = [P]
@@ -112,7 +115,8 @@ def lib(build_if_missing: bool = False):
     L.abft_destroy.argtypes = [P]
     L.abft_destroy.restype = None
     for name in ("abft_init", "abft_step", "abft_verify", "abft_correct", "abft_inject", "abft_inject_list",
-                 "abft_events", "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels"):
+                 "abft_events", "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
+                 "abft_read_checksums", "abft_selftest_wait"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -164,6 +168,14 @@ def abft_sweep_checksums_static(u_in: int, C: int, u_out: int, a_out: int, b_out
     nx, ny, nz = shape
     c = _coeffs(co)
     return f(u_in, C, u_out, a_out, b_out, nx, ny, nz, pitch, ct.byref(c), stream)
+
+
+def abft_selftest_wait(which: int, limit_us: int, stream: int = 0):
+    """Make one bounded device wait run out (0: grid barrier, 1: mbarrier); returns
+    (status, elapsed_ms)."""
+    ms = ct.c_double()
+    st = lib().abft_selftest_wait(which, limit_us, ct.c_void_p(stream), ct.byref(ms))
+    return st, ms.value
 
 
 def abft_status_string(s: int) -> str:
@@ -262,6 +274,13 @@ class Context:
         ptr = out.data_ptr() if isinstance(out, self._torch.Tensor) else out.ctypes.data
         self._check(lib().abft_read(self.h, grid, ct.c_void_p(ptr)), "abft_read")
         return out
+
+    def read_checksums(self, grid: int = 0):
+        nx, ny, nz = self.shapes[grid]
+        a = np.empty((nz, nx), dtype=np.float64)
+        b = np.empty((nz, ny), dtype=np.float64)
+        self._check(lib().abft_read_checksums(self.h, grid, a.ctypes.data, b.ctypes.data), "abft_read_checksums")
+        return a, b
 
     def current(self, grid: int = 0):
         p = ct.c_void_p()

@@ -62,7 +62,8 @@ bool valid_options(const abft_options& o) {
   return o.eps > 0 && std::isfinite(o.eps) && o.delta >= 1 && o.acc >= 0 && o.acc <= 2 &&
          o.event_capacity >= 1 && o.graph_steps >= 0 && o.max_flips_per_step >= 0 &&
          o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
-         (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1);
+         (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
+         (o.track_residual == 0 || o.track_residual == 1);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -777,6 +778,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.px = (int)align_up(G.nx, 32);
     g.ty = pick_ty(*opt, G);
     g.shallow = is_shallow(*opt, G) ? 1 : 0;
+    g.track = opt->track_residual;
     g.ntx = (G.nx + kTX - 1) / kTX;
     g.nty = (G.ny + g.ty - 1) / g.ty;
     g.pa_stride = g.ntx * kTX;
@@ -1042,6 +1044,18 @@ abft_status abft_read(abft_ctx* ctx, int32_t grid, float* dst) {
   return ABFT_OK;
 }
 
+abft_status abft_read_checksums(abft_ctx* ctx, int32_t grid, double* a, double* b) {
+  if (!ctx || !a || !b || grid < 0 || grid >= ctx->n) return ABFT_E_INVAL;
+  abft_status s = ensure_checksums(ctx, grid);
+  if (s) return s;
+  const GridDev& g = ctx->g[grid];
+  const int c = ctx->cur[grid];
+  CK(cudaMemcpyAsync(a, g.A[c], sizeof(double) * g.nz * g.nx, cudaMemcpyDefault, ctx->stream));
+  CK(cudaMemcpyAsync(b, g.B[c], sizeof(double) * g.nz * g.ny, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ABFT_OK;
+}
+
 abft_status abft_current(abft_ctx* ctx, int32_t grid, float** dev_ptr, int64_t* pitch) {
   if (!ctx || !dev_ptr || !pitch || grid < 0 || grid >= ctx->n) return ABFT_E_INVAL;
   *dev_ptr = ctx->g[grid].u[ctx->cur[grid]];
@@ -1058,6 +1072,13 @@ abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out) {
   for (int gi = 0; gi < ctx->n; ++gi) dev_rollbacks += ctx->h_gctrl[gi].rollbacks;
   out->rollbacks = ctx->rollbacks + dev_rollbacks;
   out->flips_scheduled = ctx->flips_scheduled;
+  double mr = 0.0;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    double v;
+    memcpy(&v, &ctx->h_gctrl[gi].max_resid, sizeof v);
+    mr = std::max(mr, v);
+  }
+  out->max_residual = mr;
   return ABFT_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int kSchedSteps = 4096; // sweeps covered by one uploaded schedule chu
 constexpr int kShallowMaxZ = 16;  // grids this shallow are swept with whole-column tiles
 constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side mbarrier wait loop
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // grid barrier wait bound
+constexpr unsigned long long kWaitTimeoutNs = 4ull * 1000 * 1000 * 1000;     // mbarrier wait bound
 
 // sticky device status bits
 enum : unsigned {
@@ -60,6 +61,7 @@ struct DevGridCtrl {
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
+  unsigned long long max_resid;   // bits of the largest |a'-a|/|a| of a passing entry (when tracked)
 };
 
 // everything a kernel needs to know about one grid (passed by value)
@@ -70,6 +72,7 @@ struct GridDev {
   int pb_stride;            // row stride of the b-partials (ny rounded up to a multiple of 4)
   int acc;                  // abft_acc
   int shallow;              // 1: whole-column tiles (all nz planes staged at once)
+  int track;                // 1: keep the running maximum of the passing residuals
   int gid;
   Coef k;
   double eps;

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kCheckThreads)
   unsigned long long nf = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += gridDim.x * blockDim.x) {
     if (i < na) {
+      note_resid(g, ap[i], a[i]);
       if (fails(ap[i], a[i], g.eps)) {
         const int z = i / g.nx;
         append_fail(g, z, 0, i - z * g.nx);
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(kCheckThreads)
       }
     } else {
       const int j = i - na;
+      note_resid(g, bp[j], b[j]);
       if (fails(bp[j], b[j], g.eps)) {
         const int z = j / g.ny;
         append_fail(g, z, 1, j - z * g.ny);

@@ -153,6 +153,14 @@ __device__ __forceinline__ bool fails(double pred, double comp, double eps) {
   return !(fabs(pred - comp) <= eps * fabs(comp));
 }
 
+// the running maximum of |pred - comp| / |comp| over passing entries (a non-negative
+// double's bits order like its value, so an integer maximum suffices)
+__device__ __forceinline__ void note_resid(const GridDev& g, double pred, double comp) {
+  if (!g.track) return;
+  const double rel = fabs(pred - comp) / fabs(comp);
+  if (rel <= g.eps) atomicMax(&g.gc->max_resid, (unsigned long long)__double_as_longlong(rel));
+}
+
 __device__ __forceinline__ void append_fail(const GridDev& g, int z, int which, int idx,
                                             unsigned* any = nullptr) {
   const int k = atomicAdd(&g.fcnt[2 * z + which], 1);
@@ -331,6 +339,7 @@ __device__ __forceinline__ void check_entry(const GridDev& g, int in, int out, i
     const double p = predict_a(g, g.A[in], g.u[in], z, x);
     g.AP[0][i] = p;
     if (fails(p, s, g.eps)) append_fail(g, z, 0, x, any);
+    note_resid(g, p, s);
   } else {
     const int j = i - na;
     const int z = j / g.ny, y = j - z * g.ny;
@@ -339,6 +348,7 @@ __device__ __forceinline__ void check_entry(const GridDev& g, int in, int out, i
     const double p = predict_b(g, g.B[in], g.u[in], z, y);
     g.BP[0][j] = p;
     if (fails(p, s, g.eps)) append_fail(g, z, 1, y, any);
+    note_resid(g, p, s);
   }
 }
 
@@ -480,6 +490,7 @@ struct CheckRound {
         g.A[out][e] = s;
         g.AP[0][e] = p;
         if (fails(p, s, g.eps)) append_fail(g, z, 0, x, any);
+        note_resid(g, p, s);
       } else {
         const int b = e - na;
         const int z = b / g.ny, y = b - z * g.ny;
@@ -489,6 +500,7 @@ struct CheckRound {
         g.B[out][b] = s;
         g.BP[0][b] = p;
         if (fails(p, s, g.eps)) append_fail(g, z, 1, y, any);
+        note_resid(g, p, s);
       }
     }
     __syncthreads();

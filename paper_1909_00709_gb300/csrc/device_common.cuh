@@ -152,7 +152,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // time; on timeout, or when another CTA has already timed out, the status word
 // records it and the barrier returns false, so a broken launch winds down instead
 // of hanging.  All threads of every block must call it.
-__device__ __forceinline__ bool grid_barrier(unsigned long long* count, DevCtrl* ctrl) {
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, DevCtrl* ctrl,
+                                             unsigned long long limit_ns = kBarrierTimeoutNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, DevCtrl*
       if ((spins & 1023u) == 1023u) {
         const unsigned long long t = globaltimer_ns();
         if (t0 == 0) t0 = t;
-        if (t - t0 > kBarrierTimeoutNs || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
+        if (t - t0 > limit_ns || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
           set_status(ctrl, kStTimeout);
           ok = 0;
           break;
@@ -187,10 +188,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// Wait for phase `parity` of the barrier to complete; gives up after kSpinLimit polls
-// and reports it through the status word instead of hanging.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, DevCtrl* ctrl) {
+// Wait for phase `parity` of the barrier to complete; gives up after `limit_ns` of
+// global time (or kSpinLimit polls, whichever comes first) and reports it through the
+// status word instead of hanging.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, DevCtrl* ctrl,
+                                          unsigned long long limit_ns = kWaitTimeoutNs) {
   const uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
   for (unsigned i = 0; i < kSpinLimit; ++i) {
     uint32_t done;
     asm volatile(
@@ -199,6 +203,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, DevCtr
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 255u) == 255u) {
+      const unsigned long long t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > limit_ns) break;
+    }
   }
   set_status(ctrl, kStTimeout);
   return false;

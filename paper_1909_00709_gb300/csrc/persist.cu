@@ -176,6 +176,7 @@ __device__ __forceinline__ void check_warp_round(const PersistArgs& a, const Gri
     g.BP[0][(size_t)z * len + idx] = p;
   }
   if (fails(p, s, g.eps)) append_fail(g, z, is_a ? 0 : 1, idx, any);
+  note_resid(g, p, s);
 }
 
 // flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
@@ -434,11 +435,13 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
           const double sum = reduce_a<ACC>(g, z, x, 0);
           g.A[fin][i] = sum;
           nf += fails(__ldcg(pa + i), sum, g.eps) ? 1u : 0u;
+          note_resid(g, __ldcg(pa + i), sum);
         } else {
           const int b = (int)(i - na), z = b / g.ny, y = b - z * g.ny;
           const double sum = reduce_b<ACC>(g, z, y, 0);
           g.B[fin][b] = sum;
           nf += fails(__ldcg(pb + b), sum, g.eps) ? 1u : 0u;
+          note_resid(g, __ldcg(pb + b), sum);
         }
       }
       if (nf) atomicAdd(&g.gc->fails[attempt], nf);
