@@ -98,6 +98,10 @@ typedef struct {
                                at once); 0: always stream the planes */
   int32_t track_residual;   /* 1: keep the largest relative residual |a'-a|/|a| of the entries
                                that pass (abft_counters.max_residual); costs one atomic per entry */
+  int32_t batch;            /* 1: a context with several grids advances them all with one sweep
+                               launch per tile class and one check launch per sweep (CUDA graphs
+                               of graph_steps sweeps); 0: grid by grid. Offline steps always go
+                               grid by grid. */
   void* stream;             /* cudaStream_t used for all device work */
 } abft_options;
 
@@ -210,6 +214,24 @@ ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, d
 
 ABFT_API const char* abft_last_error(const abft_ctx* ctx);
 ABFT_API const char* abft_status_string(abft_status s);
+
+/* Autotuner: time short fault-free runs of every distinct launch configuration for
+   these grids and `mode` (rows per tile 8/16/32, whole-column tiles on/off,
+   persistent launches on/off, batched launches on/off for several grids) and return
+   the fastest. Every candidate runs through abft_init/abft_step/abft_destroy on the
+   caller's device `workspace` (at least abft_tune_workspace_bytes, which is 0 for
+   invalid arguments) and the caller's inputs (same meaning as for abft_init), on
+   base->stream; `sweeps` (1..100000) are timed after 2 warm-up sweeps. *best receives
+   *base with tile_y, shallow, persistent and batch set to the winner's;
+   *best_us_per_sweep its time. Results are cached per (shapes, mode, acc, delta,
+   sweeps, track_residual) for the process: a repeated call returns at once.
+   Errors: ABFT_E_INVAL (arguments), ABFT_E_NOMEM (no candidate fits the workspace),
+   or the first failing call's status. */
+ABFT_API size_t abft_tune_workspace_bytes(const abft_grid* grids, int32_t n_grids, const abft_options* base);
+ABFT_API abft_status abft_tune(const abft_grid* grids, int32_t n_grids, const float* const* temp,
+                               const float* const* power, const abft_coeffs* coeffs, const abft_options* base,
+                               int32_t mode, int32_t sweeps, void* workspace, size_t workspace_bytes,
+                               abft_options* best, double* best_us_per_sweep);
 
 /* Self-test of failure detection without a fault: make one bounded device wait run out
    on purpose and report how it ended.

@@ -27,7 +27,7 @@ EXPORTS = ("abft_default_options", "abft_workspace_bytes", "abft_init", "abft_st
            "abft_correct", "abft_inject", "abft_inject_list", "abft_schedule", "abft_events",
            "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
            "abft_last_error", "abft_status_string", "abft_destroy", "abft_sweep_checksums_static",
-           "abft_read_checksums", "abft_selftest_wait")
+           "abft_read_checksums", "abft_selftest_wait", "abft_tune_workspace_bytes", "abft_tune")
 
 
 class abft_grid(ct.Structure):
@@ -42,7 +42,7 @@ class abft_options(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
-                ("track_residual", ct.c_int32), ("stream", ct.c_void_p)]
+                ("track_residual", ct.c_int32), ("batch", ct.c_int32), ("stream", ct.c_void_p)]
 
 
 class abft_counters(ct.Structure):
@@ -106,6 +106,11 @@ def lib(build_if_missing: bool = False):
     L.abft_current.argtypes = [P, I32, ct.POINTER(P), ct.POINTER(I64)]
     L.abft_read_checksums.argtypes = [P, I32, P, P]
     L.abft_selftest_wait.argtypes = [I32, I64, P, ct.POINTER(ct.c_double)]
+    L.abft_tune_workspace_bytes.argtypes = [ct.POINTER(abft_grid), I32, ct.POINTER(abft_options)]
+    L.abft_tune_workspace_bytes.restype = ct.c_size_t
+    L.abft_tune.argtypes = [ct.POINTER(abft_grid), I32, ct.POINTER(P), ct.POINTER(P), ct.POINTER(abft_coeffs),
+                            ct.POINTER(abft_options), I32, I32, P, ct.c_size_t, ct.POINTER(abft_options),
+                            ct.POINTER(ct.c_double)]
     L.abft_get_counters.argtypes = [P, ct.POINTER(abft_counters)]
     L.abft_time_kernels.argtypes = [P, I64, I32, P, P]
     L.abft_last_error.argtypes = [P]
@@ -116,7 +121,7 @@ def lib(build_if_missing: bool = False):
     L.abft_destroy.restype = None
     for name in ("abft_init", "abft_step", "abft_verify", "abft_correct", "abft_inject", "abft_inject_list",
                  "abft_events", "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
-                 "abft_read_checksums", "abft_selftest_wait"):
+                 "abft_read_checksums", "abft_selftest_wait", "abft_tune"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -176,6 +181,41 @@ def abft_selftest_wait(which: int, limit_us: int, stream: int = 0):
     ms = ct.c_double()
     st = lib().abft_selftest_wait(which, limit_us, ct.c_void_p(stream), ct.byref(ms))
     return st, ms.value
+
+
+def abft_tune_workspace_bytes(shapes, opt: abft_options) -> int:
+    return lib().abft_tune_workspace_bytes(_grids(shapes), len(shapes), ct.byref(opt))
+
+
+OPTION_KEYS = ("tile_y", "shallow", "persistent", "batch")
+
+
+def autotune(shapes, temps, powers, coeffs, mode: int, sweeps: int = 20, *, device=None, stream=None, **opt_kw):
+    """abft_tune on device buffers allocated here: returns (options dict for Context,
+    microseconds per sweep of the winner)."""
+    import torch
+    shapes = [tuple(int(v) for v in s) for s in shapes]
+    n = len(shapes)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    base = abft_default_options(**opt_kw)
+    base.stream = st.cuda_stream
+    nbytes = abft_tune_workspace_bytes(shapes, base)
+    if nbytes == 0:
+        raise AbftError(1, "invalid grid shapes or options")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    keep = [np.ascontiguousarray(a, dtype=np.float32) for a in list(temps) + list(powers)]
+    tp = (ct.c_void_p * n)(*[keep[i].ctypes.data for i in range(n)])
+    pp = (ct.c_void_p * n)(*[keep[n + i].ctypes.data for i in range(n)])
+    cos = (abft_coeffs * n)(*[_coeffs(c) for c in coeffs])
+    best = abft_options()
+    us = ct.c_double()
+    with torch.cuda.device(dev):
+        r = lib().abft_tune(_grids(shapes), n, tp, pp, cos, ct.byref(base), mode, sweeps,
+                            ct.c_void_p(ws.data_ptr()), nbytes, ct.byref(best), ct.byref(us))
+    if r != 0:
+        raise AbftError(r, "abft_tune failed")
+    return {k: getattr(best, k) for k in OPTION_KEYS}, us.value
 
 
 def abft_status_string(s: int) -> str:

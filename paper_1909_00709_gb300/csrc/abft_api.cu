@@ -40,6 +40,7 @@ struct GridPlan {
 struct Plan {
   std::vector<GridPlan> g;
   size_t ctrl, gctrl, events, flips, off, total;
+  size_t bgrid, btmap, broles, bints;  // batched launches: descriptors, tensor maps, roles, work lists
   int64_t sched_cap;
 };
 
@@ -63,7 +64,7 @@ bool valid_options(const abft_options& o) {
          o.event_capacity >= 1 && o.graph_steps >= 0 && o.max_flips_per_step >= 0 &&
          o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
-         (o.track_residual == 0 || o.track_residual == 1);
+         (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -98,6 +99,10 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
   P->sched_cap = std::max<int64_t>(1 << 16, (int64_t)o.max_flips_per_step * n * 64);
   P->flips = b.take(sizeof(DevFlip) * P->sched_cap);
   P->off = b.take(sizeof(int) * (kSchedSteps + 1));
+  P->bgrid = b.take(sizeof(GridDev) * n);
+  P->btmap = b.take(sizeof(CUtensorMap) * 4 * n);
+  P->broles = b.take(sizeof(BatchRole) * n);
+  P->bints = b.take(sizeof(int) * (4 * (size_t)n + 16));
   P->total = align_up(b.off, 256);
   return true;
 }
@@ -267,6 +272,23 @@ struct abft_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;
   size_t ev_used = 0;
+  // batched launches (contexts with several grids)
+  struct BClass {
+    int shallow, ty, smem, blocks, n, grids_at, off_at;
+  };
+  std::vector<BClass> bcls;      // sweep launches, one per tile class
+  BClass bchk{};                 // the check launch
+  GridDev* d_bgrid = nullptr;
+  CUtensorMap* d_btmap = nullptr;
+  BatchRole* d_roles = nullptr;
+  int* d_bints = nullptr;
+  std::vector<int> h_bints;
+  std::vector<CUtensorMap> h_btmap;
+  BatchRole* h_roles = nullptr;  // pinned
+  cudaEvent_t roles_ev = nullptr;
+  bool roles_pending = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [unprotected, online]: graph_steps sweeps each
   // counters
   int64_t launches = 0, rollbacks = 0, flips_scheduled = 0;
   unsigned status_seen = 0;
@@ -509,6 +531,177 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
   return ABFT_OK;
 }
 
+// Work lists of the batched launches: grids grouped by tile class, deepest first;
+// the check launch takes one block per kBatchRounds rounds of 32 entries of a grid.
+void build_batch_tables(abft_ctx* ctx) {
+  const int n = ctx->n;
+  ctx->h_btmap.resize(4 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) ctx->h_btmap[4 * i + k] = ctx->tm_u[3 * i + k];
+    ctx->h_btmap[4 * i + 3] = ctx->tm_c[i];
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const GridDev &x = ctx->g[a], &y = ctx->g[b];
+    if (x.nz != y.nz) return x.nz > y.nz;
+    return x.ntx * x.nty > y.ntx * y.nty;
+  });
+  std::vector<int> grids, offs;
+  ctx->bcls.clear();
+  std::vector<std::pair<int, int>> classes;  // (shallow, ty) in first-seen order
+  for (int i : order) {
+    const std::pair<int, int> c(ctx->g[i].shallow, ctx->g[i].ty);
+    if (std::find(classes.begin(), classes.end(), c) == classes.end()) classes.push_back(c);
+  }
+  std::vector<std::pair<size_t, size_t>> at;
+  std::vector<std::vector<int>> off_lists;
+  for (const auto& c : classes) {
+    abft_ctx::BClass b{};
+    b.shallow = c.first;
+    b.ty = c.second;
+    b.grids_at = (int)grids.size();
+    std::vector<int> off{0};
+    for (int i : order) {
+      const GridDev& g = ctx->g[i];
+      if (g.shallow != c.first || g.ty != c.second) continue;
+      grids.push_back(i);
+      off.push_back(off.back() + g.ntx * g.nty);
+      b.smem = std::max(b.smem, batch_sweep_smem(g.shallow, g.ty, g.nz));
+    }
+    b.n = (int)off.size() - 1;
+    b.blocks = off.back();
+    off_lists.push_back(off);
+    ctx->bcls.push_back(b);
+  }
+  abft_ctx::BClass& k = ctx->bchk;
+  k = abft_ctx::BClass{};
+  k.grids_at = (int)grids.size();
+  std::vector<int> koff{0};
+  for (int i = 0; i < n; ++i) {
+    const GridDev& g = ctx->g[i];
+    grids.push_back(i);
+    const int64_t rounds = ((int64_t)g.nz * (g.nx + g.ny) + 31) / 32;
+    koff.push_back(koff.back() + (int)((rounds + kBatchRounds - 1) / kBatchRounds));
+  }
+  k.n = n;
+  k.blocks = koff.back();
+  off_lists.push_back(koff);
+  ctx->h_bints = grids;
+  for (size_t c = 0; c < off_lists.size(); ++c) {
+    abft_ctx::BClass& b = c < ctx->bcls.size() ? ctx->bcls[c] : ctx->bchk;
+    b.off_at = (int)ctx->h_bints.size();
+    ctx->h_bints.insert(ctx->h_bints.end(), off_lists[c].begin(), off_lists[c].end());
+  }
+}
+
+BatchArgs batch_args(const abft_ctx* ctx, const abft_ctx::BClass& b) {
+  BatchArgs a;
+  a.g = ctx->d_bgrid;
+  a.tm = ctx->d_btmap;
+  a.roles = ctx->d_roles;
+  a.grids = ctx->d_bints + b.grids_at;
+  a.off = ctx->d_bints + b.off_at;
+  a.n = b.n;
+  return a;
+}
+
+int batch_kernels_per_sweep(const abft_ctx* ctx, bool prot) {
+  int k = 0;
+  for (const auto& b : ctx->bcls) k += b.blocks > 0;
+  return k + (prot && ctx->bchk.blocks > 0 ? 1 : 0);
+}
+
+// one sweep of every grid: the class sweeps, then the check; `counted` routes the
+// launches through run() (counting and timing), otherwise they are being captured
+cudaError_t batch_sweep(abft_ctx* ctx, const Launch& L, bool prot, bool counted) {
+  const int acc = ctx->opt.acc;
+  for (const auto& b : ctx->bcls) {
+    const BatchArgs a = batch_args(ctx, b);
+    auto f = [&] { return launch_sweep_batch(L, a, b.blocks, b.smem, b.shallow, b.ty, prot, acc); };
+    const cudaError_t e = counted ? run(ctx, prot ? kKSweepProt : kKSweepPlain, f) : f();
+    if (e != cudaSuccess) return e;
+  }
+  if (!prot) return cudaSuccess;
+  const BatchArgs a = batch_args(ctx, ctx->bchk);
+  auto f = [&] { return launch_check_batch(L, a, ctx->bchk.blocks, acc); };
+  return counted ? run(ctx, kKCheckOnline, f) : f();
+}
+
+// a CUDA graph of graph_steps batched sweeps, captured on a private stream
+abft_status batch_graph(abft_ctx* ctx, bool prot, cudaGraphExec_t* out) {
+  if (ctx->graph[prot]) {
+    *out = ctx->graph[prot];
+    return ABFT_OK;
+  }
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  Launch L = launcher(ctx);
+  L.s = ctx->cap_stream;
+  CK(cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < ctx->opt.graph_steps && e == cudaSuccess; ++t) e = batch_sweep(ctx, L, prot, false);
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(L.s, &gr);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph[prot], gr, 0);
+  if (gr) cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(ctx, ABFT_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  *out = ctx->graph[prot];
+  return ABFT_OK;
+}
+
+// `n` sweeps of every grid with batched launches (graphs of graph_steps sweeps where
+// they fit, single sweeps for the rest)
+abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
+  const bool prot = mode == ABFT_MODE_ONLINE;
+  if (prot)
+    for (int gi = 0; gi < ctx->n; ++gi) {
+      abft_status s = ensure_checksums(ctx, gi);
+      if (s) return s;
+    }
+  for (const auto& b : ctx->bcls) CK(batch_prepare(b.shallow, b.ty, prot, ctx->opt.acc, b.smem));
+  if (ctx->roles_pending) CK(cudaEventSynchronize(ctx->roles_ev));  // the previous upload has been read
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    BatchRole& r = ctx->h_roles[gi];
+    const int c = ctx->cur[gi], ref = ctx->ref[gi];
+    r.s0 = ctx->step;
+    r.first = c;
+    r.mode = prot ? 1 : 0;
+    r.a = other_than(c, ref);
+    r.b = c == ref ? other_than(ref, r.a) : c;
+  }
+  CK(cudaMemcpyAsync(ctx->d_roles, ctx->h_roles, sizeof(BatchRole) * ctx->n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(ctx->roles_ev, ctx->stream));
+  ctx->roles_pending = true;
+  const Launch L = launcher(ctx);
+  int64_t k = 0;
+  const int T = ctx->opt.graph_steps;
+  if (T > 0 && !ctx->timing && n >= T) {
+    cudaGraphExec_t ex = nullptr;
+    abft_status s = batch_graph(ctx, prot, &ex);
+    if (s) return s;
+    for (; n - k >= T; k += T) {
+      CK(cudaGraphLaunch(ex, ctx->stream));
+      ctx->launches += (int64_t)T * batch_kernels_per_sweep(ctx, prot);
+    }
+  }
+  for (; k < n; ++k) CK(batch_sweep(ctx, L, prot, true));
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    const BatchRole& r = ctx->h_roles[gi];
+    if (prot) {
+      ctx->cur[gi] = (int)((r.first + n) % 3);
+      ctx->ref[gi] = ctx->cur[gi];
+      ctx->ref_step[gi] = ctx->step + n;
+      ctx->ck_valid[gi] = 1;
+    } else {
+      ctx->cur[gi] = ((n - 1) & 1) ? r.b : r.a;
+      ctx->ck_valid[gi] = 0;
+    }
+  }
+  ctx->step += n;
+  return ABFT_OK;
+}
+
 abft_status status_from_device(abft_ctx* ctx) {
   const unsigned st = ctx->h_ctrl->status;
   ctx->status_seen |= st;
@@ -666,6 +859,7 @@ void abft_default_options(abft_options* o) {
   o->acc = ABFT_ACC_FP32;
   o->event_capacity = 4096;
   o->graph_steps = 50;
+  o->batch = 1;
   o->tile_y = 0;
   o->max_flips_per_step = 64;
   o->persistent = 1;
@@ -719,6 +913,11 @@ void abft_destroy(abft_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (cudaGraphExec_t& x : ctx->graph)
+    if (x) cudaGraphExecDestroy(x);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->roles_ev) cudaEventDestroy(ctx->roles_ev);
+  if (ctx->h_roles) cudaFreeHost(ctx->h_roles);
   if (ctx->h_flips) cudaFreeHost(ctx->h_flips);
   if (ctx->h_off) cudaFreeHost(ctx->h_off);
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
@@ -760,13 +959,19 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   ctx->events = (abft_event*)(ws + P.events);
   ctx->d_flips = (DevFlip*)(ws + P.flips);
   ctx->d_off = (int*)(ws + P.off);
+  ctx->d_bgrid = (GridDev*)(ws + P.bgrid);
+  ctx->d_btmap = (CUtensorMap*)(ws + P.btmap);
+  ctx->d_roles = (BatchRole*)(ws + P.broles);
+  ctx->d_bints = (int*)(ws + P.bints);
   ctx->sched_cap = P.sched_cap;
   if (cudaMallocHost(&ctx->h_flips, sizeof(DevFlip) * P.sched_cap) != cudaSuccess ||
       cudaMallocHost(&ctx->h_off, sizeof(int) * (kSchedSteps + 1)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_gctrl, sizeof(DevGridCtrl) * n_grids) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_ev, sizeof(abft_event)) != cudaSuccess)
+      cudaMallocHost(&ctx->h_ev, sizeof(abft_event)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_roles, sizeof(BatchRole) * n_grids) != cudaSuccess)
     return bail(ABFT_E_NOMEM);
+  if (cudaEventCreateWithFlags(&ctx->roles_ev, cudaEventDisableTiming) != cudaSuccess) return bail(ABFT_E_CUDA);
   memset(ctx->h_ctrl, 0, sizeof(DevCtrl));
   memset(ctx->h_gctrl, 0, sizeof(DevGridCtrl) * n_grids);
   for (int i = 0; i < n_grids; ++i) {
@@ -840,6 +1045,11 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
       return bail(st);
     }
   }
+  build_batch_tables(ctx);
+  CKI(cudaMemcpyAsync(ctx->d_bgrid, ctx->g.data(), sizeof(GridDev) * n_grids, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_btmap, ctx->h_btmap.data(), sizeof(CUtensorMap) * ctx->h_btmap.size(),
+                      cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_bints, ctx->h_bints.data(), sizeof(int) * ctx->h_bints.size(), cudaMemcpyHostToDevice, s));
   ctx->h_ctrl->ev_cap = opt->event_capacity;
   ctx->h_ctrl->inject_enabled = 1;
   CKI(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, s));
@@ -914,6 +1124,11 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
       } else {
         s = offline_window(ctx, covered);
       }
+      if (s) return s;
+      continue;
+    }
+    if (ctx->opt.batch && ctx->n > 1 && covered > 0) {
+      s = batch_all(ctx, covered, mode);
       if (s) return s;
       continue;
     }

@@ -143,4 +143,31 @@ bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);
 
+// ------------------------------------------------------------ batched grids
+// Buffer roles of sweep s of one grid in a batched run that started at sweep s0.
+// mode 1 (protected): in = (first + s - s0) mod 3, out = in + 1 mod 3.
+// mode 0 (unprotected): sweep s0 reads `first` and writes `a`; later sweeps go
+// a -> b at odd offsets and b -> a at even ones.
+struct BatchRole {
+  long long s0;
+  int first, a, b, mode;
+};
+
+// one batched launch: the blocks of `n` grids, grid grids[i] owning blocks
+// off[i] .. off[i+1]-1 (all arrays in device memory)
+struct BatchArgs {
+  const GridDev* g;          // [n_grids]
+  const CUtensorMap* tm;     // [n_grids][4]: u[0], u[1], u[2], C
+  const BatchRole* roles;    // [n_grids]
+  const int* grids;
+  const int* off;            // [n + 1]
+  int n;
+};
+constexpr int kBatchRounds = 8;  // 32-entry check rounds per block of the batched check
+int batch_sweep_smem(int shallow, int ty, int nz);
+cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int smem);
+cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, int smem, int shallow, int ty,
+                               bool prot, int acc);
+cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc);
+
 }  // namespace abft

@@ -21,11 +21,7 @@ __global__ void __launch_bounds__(kCheckThreads)
     k_check_online(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
   const int n = g.nz * (g.nx + g.ny);
   __shared__ CheckShared sh;
-  for (int base = blockIdx.x * 32; base < n; base += gridDim.x * 32) {  // 32 entries per block round
-    CheckRound<ACC> c;
-    c.load(g, in, 0, base, n);
-    c.finish(g, out, 0, nullptr, sh);
-  }
+  check_rounds<ACC>(g, in, out, blockIdx.x * 32, gridDim.x * 32, n, sh);  // 32 entries per block round
   double* Aout = g.A[out];
   double* Bout = g.B[out];
   const float* uin = g.u[in];
@@ -155,8 +151,22 @@ static int check_blocks(const GridDev& g, int lanes = 1) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// multiprocessors of the current device (cached per device)
+static int sm_count() {
+  static int cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out) {
-  const int blocks = (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + 31) / 32, 65535);
+  // one 32-entry round per block up to a full wave of 8 blocks per SM, pipelined rounds beyond
+  const int blocks = (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + 31) / 32, 8LL * sm_count());
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: k_check_online<ABFT_ACC_TWOSUM><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
     case ABFT_ACC_FP64: k_check_online<ABFT_ACC_FP64><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;

@@ -507,4 +507,27 @@ struct CheckRound {
   }
 };
 
+// Rounds base0, base0 + stride, ... (below n) of the online check by one block; the
+// loads of the next round are issued before the current round is finished, so one
+// round's memory latency hides behind the other's reduction.
+template <int ACC>
+__device__ __forceinline__ void check_rounds(const GridDev& g, int in, int out, int base0, int stride, int n,
+                                             CheckShared& sh) {
+  CheckRound<ACC> ca, cb;
+  int b = base0;
+  if (b >= n) return;
+  ca.load(g, in, 0, b, n);
+  for (;;) {
+    const int b1 = b + stride;
+    if (b1 < n) cb.load(g, in, 0, b1, n);
+    ca.finish(g, out, 0, nullptr, sh);
+    if (b1 >= n) return;
+    const int b2 = b1 + stride;
+    if (b2 < n) ca.load(g, in, 0, b2, n);
+    cb.finish(g, out, 0, nullptr, sh);
+    if (b2 >= n) return;
+    b = b2;
+  }
+}
+
 }  // namespace abft

@@ -155,6 +155,77 @@ struct AccA<ABFT_ACC_FP64> {
   }
 };
 
+// --------------------------------------------- multi-row reduction of row partials
+// R rows (R = 2, 4, 8 or 16) held by every lane of a warp, one lane-partial per row, are
+// reduced to R row totals with log2(R) halving exchanges (offsets 16, 8, ...) and
+// butterfly exchanges for the remaining offsets.  Every stage pairs lanes l and l^o,
+// the same pairs, in the same stage order, as the per-row butterfly of row_store, and
+// each stage's addition is commutative, so every row total is bit-identical to
+// row_store's.  Lane l ends holding row (l >> (5 - log2 R)).
+template <int ACC>
+struct RowPart;
+template <>
+struct RowPart<ABFT_ACC_FP32> {
+  using T = float;
+  __device__ static T of(const float (&m)[4]) { return ((m[0] + m[1]) + m[2]) + m[3]; }
+  __device__ static T comb(T a, T b) { return a + b; }
+  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<float*>(PB)[i] = v; }
+};
+template <>
+struct RowPart<ABFT_ACC_TWOSUM> {
+  using T = float2;
+  __device__ static T of(const float (&m)[4]) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc2(hi, lo, m[i]);
+    return make_float2(hi, lo);
+  }
+  __device__ static T comb(T a, T b) {  // as warp_sum2: two_sum(a.hi, b.hi), lo = a.lo + b.lo + e
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return make_float2(s, a.y + b.y + e);
+  }
+  __device__ static T shfl(T v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+  }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<float2*>(PB)[i] = v; }
+};
+template <>
+struct RowPart<ABFT_ACC_FP64> {
+  using T = double;
+  __device__ static T of(const float (&m)[4]) { return (((double)m[0] + (double)m[1]) + (double)m[2]) + (double)m[3]; }
+  __device__ static T comb(T a, T b) { return a + b; }
+  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  __device__ static void store(void* PB, size_t i, T v) { static_cast<double*>(PB)[i] = v; }
+};
+
+template <int ACC, int R>
+__device__ __forceinline__ typename RowPart<ACC>::T reduce_rows(typename RowPart<ACC>::T (&v)[R], int lane) {
+  using RP = RowPart<ACC>;
+  static_assert(R == 2 || R == 4 || R == 8 || R == 16, "row count");
+  constexpr int L = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));  // halving stages
+  int cnt = R;
+#pragma unroll
+  for (int st = 0; st < L; ++st) {
+    const int o = 16 >> st;
+    const bool up = (lane & o) != 0;  // keeps the upper half of its current rows
+    cnt >>= 1;
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      if (i < cnt) {
+        const typename RP::T send = up ? v[i] : v[i + cnt];
+        const typename RP::T keep = up ? v[i + cnt] : v[i];
+        v[i] = RP::comb(keep, RP::shfl(send, o));
+      }
+    }
+  }
+  typename RP::T t = v[0];
+#pragma unroll
+  for (int o = 16 >> L; o > 0; o >>= 1) t = RP::comb(t, RP::shfl(t, o));
+  return t;
+}
+
 // shared-memory layout of the sweep
 template <int TY>
 struct SweepSmem {
@@ -268,6 +339,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
     const float* Cs = sm.stage_c((int)((base + z) % S));
     AccA<ACC> acc;
     if (PROT) acc.zero();
+    typename RowPart<ACC>::T rp[Cfg::RPW > 1 ? Cfg::RPW : 2];
 #pragma unroll
     for (int rr = 0; rr < Cfg::RPW; ++rr) {
       const int r = warp + rr * NW;
@@ -322,9 +394,17 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
         float m[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
-        AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
+        if (Cfg::RPW == 1) AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
+        else rp[rr] = RowPart<ACC>::of(m);
         acc.add(m);
       }
+    }
+    if (PROT && Cfg::RPW > 1) {  // this warp's rows reduced together; lane (rr << SH) holds row rr
+      constexpr int SH = Cfg::RPW == 2 ? 4 : (Cfg::RPW == 4 ? 3 : 2);
+      const typename RowPart<ACC>::T tot = reduce_rows<ACC, (Cfg::RPW > 1 ? Cfg::RPW : 2)>(rp, lane);
+      const int y = y0 + warp + (lane >> SH) * NW;
+      if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny)
+        RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.pb_stride + y, tot);
     }
     if (PROT) acc.put(sm.red + (z & 1) * Cfg::RED_HALF, warp, lane);
     tile_sync();
@@ -407,77 +487,6 @@ __device__ void recompute_pb(const GridDev& g, const float* __restrict__ u, void
   for (int i = 0; i < 4; ++i)
     m[i] = (y < g.ny && gx0 + i < g.nx) ? __ldcg(u + ((size_t)z * g.ny + y) * g.px + gx0 + i) : 0.f;
   AccA<ACC>::row_store(m, PB, ((size_t)txi * g.nz + z) * g.pb_stride + y, lane == 0);
-}
-
-// --------------------------------------------- multi-row reduction of row partials
-// R rows (R = 8 or 16) held by every lane of a warp, one lane-partial per row, are
-// reduced to R row totals with log2(R) halving exchanges (offsets 16, 8, ...) and
-// butterfly exchanges for the remaining offsets.  Every stage pairs lanes l and l^o,
-// the same pairs, in the same stage order, as the per-row butterfly of row_store, and
-// each stage's addition is commutative, so every row total is bit-identical to
-// row_store's.  Lane l ends holding row (l >> (5 - log2 R)).
-template <int ACC>
-struct RowPart;
-template <>
-struct RowPart<ABFT_ACC_FP32> {
-  using T = float;
-  __device__ static T of(const float (&m)[4]) { return ((m[0] + m[1]) + m[2]) + m[3]; }
-  __device__ static T comb(T a, T b) { return a + b; }
-  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-  __device__ static void store(void* PB, size_t i, T v) { static_cast<float*>(PB)[i] = v; }
-};
-template <>
-struct RowPart<ABFT_ACC_TWOSUM> {
-  using T = float2;
-  __device__ static T of(const float (&m)[4]) {
-    float hi = 0.f, lo = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc2(hi, lo, m[i]);
-    return make_float2(hi, lo);
-  }
-  __device__ static T comb(T a, T b) {  // as warp_sum2: two_sum(a.hi, b.hi), lo = a.lo + b.lo + e
-    float s, e;
-    two_sum(a.x, b.x, s, e);
-    return make_float2(s, a.y + b.y + e);
-  }
-  __device__ static T shfl(T v, int o) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
-  }
-  __device__ static void store(void* PB, size_t i, T v) { static_cast<float2*>(PB)[i] = v; }
-};
-template <>
-struct RowPart<ABFT_ACC_FP64> {
-  using T = double;
-  __device__ static T of(const float (&m)[4]) { return (((double)m[0] + (double)m[1]) + (double)m[2]) + (double)m[3]; }
-  __device__ static T comb(T a, T b) { return a + b; }
-  __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-  __device__ static void store(void* PB, size_t i, T v) { static_cast<double*>(PB)[i] = v; }
-};
-
-template <int ACC, int R>
-__device__ __forceinline__ typename RowPart<ACC>::T reduce_rows(typename RowPart<ACC>::T (&v)[R], int lane) {
-  using RP = RowPart<ACC>;
-  static_assert(R == 8 || R == 16, "row count");
-  constexpr int L = R == 8 ? 3 : 4;  // halving stages
-  int cnt = R;
-#pragma unroll
-  for (int st = 0; st < L; ++st) {
-    const int o = 16 >> st;
-    const bool up = (lane & o) != 0;  // keeps the upper half of its current rows
-    cnt >>= 1;
-#pragma unroll
-    for (int i = 0; i < R / 2; ++i) {
-      if (i < cnt) {
-        const typename RP::T send = up ? v[i] : v[i + cnt];
-        const typename RP::T keep = up ? v[i + cnt] : v[i];
-        v[i] = RP::comb(keep, RP::shfl(send, o));
-      }
-    }
-  }
-  typename RP::T t = v[0];
-#pragma unroll
-  for (int o = 16 >> L; o > 0; o >>= 1) t = RP::comb(t, RP::shfl(t, o));
-  return t;
 }
 
 // ======================================================= shallow grids (nz <= kShallowMaxZ)

@@ -64,6 +64,28 @@ def test_workspace_bytes_validates(abi):
     assert two > abi.abft_workspace_bytes([(64, 64, 8)], o)
 
 
+def test_tune_workspace_covers_every_candidate(abi):
+    o = abi.abft_default_options()
+    for shapes in ([(64, 64, 8)], [(300, 130, 40)], [(64, 64, 8), (200, 37, 30)]):
+        need = abi.abft_tune_workspace_bytes(shapes, o)
+        for ty in (8, 16, 32):
+            for sh in (0, 1):
+                assert need >= abi.abft_workspace_bytes(shapes, abi.abft_default_options(tile_y=ty, shallow=sh))
+    assert abi.abft_tune_workspace_bytes([(0, 4, 4)], o) == 0
+    L = abi.lib()
+    best = abi.abft_options()
+    us = ct.c_double()
+    g = (abi.abft_grid * 1)(abi.abft_grid(8, 8, 2))
+    # bad mode / sweep counts are refused before any CUDA call
+    assert L.abft_tune(g, 1, None, None, None, ct.byref(o), 0, 10, None, 0, ct.byref(best), ct.byref(us)) == 1
+    tp = (ct.c_void_p * 1)(1024)
+    co = (abi.abft_coeffs * 1)()
+    assert L.abft_tune(g, 1, tp, tp, co, ct.byref(o), 3, 10, ct.c_void_p(0x1000), 1 << 20, ct.byref(best),
+                       ct.byref(us)) == 1
+    assert L.abft_tune(g, 1, tp, tp, co, ct.byref(o), 1, 0, ct.c_void_p(0x1000), 1 << 20, ct.byref(best),
+                       ct.byref(us)) == 1
+
+
 def test_init_rejects_bad_arguments_without_touching_the_gpu(abi):
     L = abi.lib()
     h = ct.c_void_p()
