@@ -516,6 +516,7 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
       const int out = (in + 1) % 3;  // the verified state moves with every sweep
       CK(run(ctx, kKSweepProt, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
       CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(L, g, in, out); }));
+      CK(run(ctx, kKOther, [&] { return launch_resolve(L, g, in, out); }));
       ctx->cur[gi] = out;
       ctx->ref[gi] = out;
       ctx->ref_step[gi] = ctx->step + 1;

@@ -57,7 +57,7 @@ struct DevGridCtrl {
   unsigned int done_aux;
   unsigned int rollbacks;   // offline windows the persistent kernel recomputed
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
-  unsigned int pad2;
+  unsigned int redo;         // persistent online kernel: 1 = every CTA recomputes the speculative sweep
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
@@ -126,6 +126,8 @@ cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& t
 cudaError_t launch_source_term(const Launch& L, const GridDev& g, const abft_coeffs& co);
 cudaError_t launch_checksums(const Launch& L, const GridDev& g, const float* u, double* A, double* B);
 cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out);
+// location and correction after launch_check_online, one block per plane
+cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out);
 cudaError_t launch_reduce_partials(const Launch& L, const GridDev& g, int out);
 cudaError_t launch_chain(const Launch& L, const GridDev& g, const double* a_in, const double* b_in,
                          double* a_out, double* b_out);
@@ -163,7 +165,7 @@ struct BatchArgs {
   const int* off;            // [n + 1]
   int n;
 };
-constexpr int kBatchRounds = 8;  // 32-entry check rounds per block of the batched check
+constexpr int kBatchRounds = 16;  // 32-entry check rounds per block of the batched check (2 per warp)
 int batch_sweep_smem(int shallow, int ty, int nz);
 cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int smem);
 cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, int smem, int shallow, int ty,

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
 }
 
 // The online check of the sweep just done (Sec. 3) for every grid of the batch:
-// each block takes pipelined rounds of 32 entries of one grid (kBatchRounds of them);
+// each block's warps take rounds of 32 entries of one grid (kBatchRounds per block);
 // that grid's last block to finish locates and corrects (Sec. 3.5).
 template <int ACC>
 __global__ void __launch_bounds__(kBatchCheckThreads)
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(kBatchCheckThreads)
   const GridDev& g = sg;
   const long long s = s_step;
   const int n = g.nz * (g.nx + g.ny);
-  __shared__ CheckShared sh;
-  check_rounds<ACC>(g, 0, 1, lb * 32, nb * 32, n, sh);
+  const int nw = kBatchCheckThreads / 32;
+  check_warps<ACC>(g, 0, 1, lb * nw + (int)(threadIdx.x >> 5), nb * nw, n);
   __shared__ int s_last;
   __threadfence();
   __syncthreads();

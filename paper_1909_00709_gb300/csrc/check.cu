@@ -14,26 +14,36 @@ constexpr int kCheckThreads = 256;
 // ------------------------------------------------------------ online check
 
 // One sweep's check (Sec. 3): reduce the partials into a^{t+1}, b^{t+1}; interpolate
-// from a^t, b^t (Theorem 1); compare (Sec. 3.4); the last block to finish locates
-// and corrects (Sec. 3.5) in place in u[out].
+// from a^t, b^t (Theorem 1); compare (Sec. 3.4).  Failing entries go to the per-plane
+// lists that k_resolve then works through.
 template <int ACC>
 __global__ void __launch_bounds__(kCheckThreads)
     k_check_online(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
+  (void)ctrl;
+  (void)ev;
   const int n = g.nz * (g.nx + g.ny);
-  __shared__ CheckShared sh;
-  check_rounds<ACC>(g, in, out, blockIdx.x * 32, gridDim.x * 32, n, sh);  // 32 entries per block round
-  double* Aout = g.A[out];
-  double* Bout = g.B[out];
-  const float* uin = g.u[in];
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&g.gc->done_check, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  resolve_planes(g, uin, g.u[out], Aout, Bout, g.AP[0], g.BP[0], g.gc->step - 1, ctrl, ev, &g.gc->unresolved);
-  if (threadIdx.x == 0) g.gc->done_check = 0;
+  const int nw = kCheckThreads / 32;
+  check_warps<ACC>(g, in, out, blockIdx.x * nw + (int)(threadIdx.x >> 5), gridDim.x * nw, n);
+}
+
+// Location and correction (Sec. 3.5) after the online check of the sweep just done,
+// one block per plane with failing entries (planes are independent): a single
+// intersection by Eq. (8), other patterns by recomputing lines from u[in].
+__global__ void __launch_bounds__(kCheckThreads)
+    k_resolve(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
+  __shared__ ResolveSmem sm;
+  __shared__ int s_hit;
+  if (threadIdx.x == 0) sm.nfix = 0;
+  const long long step = g.gc->step - 1;
+  for (int z = blockIdx.x; z < g.nz; z += gridDim.x) {
+    if (threadIdx.x == 0) s_hit = (__ldcg(&g.fcnt[2 * z]) | __ldcg(&g.fcnt[2 * z + 1])) != 0;
+    __syncthreads();
+    const bool hit = s_hit != 0;
+    __syncthreads();  // every thread has read s_hit before thread 0 rewrites it
+    if (hit)
+      resolve_plane(sm, g, g.u[in], g.u[out], g.A[out], g.B[out], g.AP[0], g.BP[0], step, ctrl, ev,
+                    &g.gc->unresolved, z);
+  }
 }
 
 // ------------------------------------------------------------ offline pieces
@@ -165,13 +175,19 @@ static int sm_count() {
 }
 
 cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out) {
-  // one 32-entry round per block up to a full wave of 8 blocks per SM, pipelined rounds beyond
-  const int blocks = (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + 31) / 32, 8LL * sm_count());
+  // 32 entries per warp, up to one wave of 8 blocks per SM; further entries by striding
+  const int blocks =
+      (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + kCheckThreads - 1) / kCheckThreads, 8LL * sm_count());
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: k_check_online<ABFT_ACC_TWOSUM><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
     case ABFT_ACC_FP64: k_check_online<ABFT_ACC_FP64><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
     default: k_check_online<ABFT_ACC_FP32><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out) {
+  k_resolve<<<std::min(g.nz, 1024), kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events);
   return cudaGetLastError();
 }
 

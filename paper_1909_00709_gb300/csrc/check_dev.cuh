@@ -25,7 +25,7 @@ __device__ __forceinline__ double load_partial(const void* p, size_t i) {
 // FP32 pairs (hi, lo) with TwoSum (error about n u^2, below FP64 rounding of the
 // total here, and at FP32 speed: GB300's FP64 rate is a small fraction of its FP32
 // rate); the pair is widened once, hi + lo in FP64.  The FP64 variant sums in FP64.
-// Every path (one thread per entry, or eight cooperating warps) evaluates exactly
+// Every path (one thread per entry, or the persistent kernel's check warp) evaluates exactly
 // this, so results agree bit for bit.
 constexpr int kLanes = 8;
 
@@ -275,9 +275,41 @@ static __device__ void sort_small(int* v, int n) {
   }
 }
 
-// Location (Sec. 3.4/3.5) for every plane with failing entries; run by one block.
-// uin == nullptr means no previous state is available: only single intersections
-// can then be corrected, other patterns are counted in ctrl->verdict.
+// Location (Sec. 3.4/3.5) of plane z, whose entries failed, by one block: its lists
+// are read (and cleared), a single intersection is corrected by Eq. (8), other
+// patterns recompute the failing lines from uin (R5).  uin == nullptr means no
+// previous state is available: only single intersections can then be corrected,
+// other patterns are counted in *unresolved.  Planes are independent, so blocks may
+// resolve different planes at the same time.
+static __device__ void resolve_plane(ResolveSmem& sm, const GridDev& g, const float* uin, float* u, double* A,
+                                     double* B, const double* ap, const double* bp, long long step, DevCtrl* ctrl,
+                                     abft_event* ev, unsigned long long* unresolved, int z) {
+  if (threadIdx.x == 0) {
+    const int ca = __ldcg(&g.fcnt[2 * z]), cb = __ldcg(&g.fcnt[2 * z + 1]);
+    sm.na = ca;
+    sm.nb = cb;
+    for (int k = 0; k < min(ca, kFCap); ++k) sm.fa[k] = __ldcg(&g.fidx[(size_t)(2 * z) * kFCap + k]);
+    for (int k = 0; k < min(cb, kFCap); ++k) sm.fb[k] = __ldcg(&g.fidx[(size_t)(2 * z + 1) * kFCap + k]);
+    sort_small(sm.fa, min(ca, kFCap));
+    sort_small(sm.fb, min(cb, kFCap));
+    g.fcnt[2 * z] = 0;
+    g.fcnt[2 * z + 1] = 0;
+  }
+  __syncthreads();
+  const bool overflow = sm.na > kFCap || sm.nb > kFCap;
+  if (sm.na == 1 && sm.nb == 1) {
+    correct_point(g, z, sm.fa[0], sm.fb[0], u, A, B, ap, bp, step, ctrl, ev, sm);
+  } else if (uin != nullptr) {
+    if (overflow && threadIdx.x == 0) set_status(ctrl, kStFailOverflow);
+    recompute_lines(g, z, uin, u, A, B, overflow, step, ctrl, ev, sm);
+  } else if (threadIdx.x == 0) {
+    atomicAdd(unresolved, 1ull);
+  }
+  __syncthreads();
+}
+
+// Location for every plane with failing entries, by one block (the fix list `sm.fix`
+// collects what was changed, for the persistent kernel's repair).
 static __device__ void resolve_planes_into(ResolveSmem& sm, const GridDev& g, const float* uin, float* u, double* A,
                                            double* B, const double* ap, const double* bp, long long step,
                                            DevCtrl* ctrl, abft_event* ev, unsigned long long* unresolved) {
@@ -288,32 +320,8 @@ static __device__ void resolve_planes_into(ResolveSmem& sm, const GridDev& g, co
     for (int j = threadIdx.x; j < zn; j += blockDim.x)
       sm.flag[j] = (__ldcg(&g.fcnt[2 * (zb + j)]) | __ldcg(&g.fcnt[2 * (zb + j) + 1])) != 0;
     __syncthreads();
-    for (int j = 0; j < zn; ++j) {
-      if (!sm.flag[j]) continue;
-      const int z = zb + j;
-      if (threadIdx.x == 0) {
-        const int ca = __ldcg(&g.fcnt[2 * z]), cb = __ldcg(&g.fcnt[2 * z + 1]);
-        sm.na = ca;
-        sm.nb = cb;
-        for (int k = 0; k < min(ca, kFCap); ++k) sm.fa[k] = __ldcg(&g.fidx[(size_t)(2 * z) * kFCap + k]);
-        for (int k = 0; k < min(cb, kFCap); ++k) sm.fb[k] = __ldcg(&g.fidx[(size_t)(2 * z + 1) * kFCap + k]);
-        sort_small(sm.fa, min(ca, kFCap));
-        sort_small(sm.fb, min(cb, kFCap));
-        g.fcnt[2 * z] = 0;
-        g.fcnt[2 * z + 1] = 0;
-      }
-      __syncthreads();
-      const bool overflow = sm.na > kFCap || sm.nb > kFCap;
-      if (sm.na == 1 && sm.nb == 1) {
-        correct_point(g, z, sm.fa[0], sm.fb[0], u, A, B, ap, bp, step, ctrl, ev, sm);
-      } else if (uin != nullptr) {
-        if (overflow && threadIdx.x == 0) set_status(ctrl, kStFailOverflow);
-        recompute_lines(g, z, uin, u, A, B, overflow, step, ctrl, ev, sm);
-      } else if (threadIdx.x == 0) {
-        atomicAdd(unresolved, 1ull);
-      }
-      __syncthreads();
-    }
+    for (int j = 0; j < zn; ++j)
+      if (sm.flag[j]) resolve_plane(sm, g, uin, u, A, B, ap, bp, step, ctrl, ev, unresolved, zb + j);
     __syncthreads();
   }
 }
@@ -352,182 +360,116 @@ __device__ __forceinline__ void check_entry(const GridDev& g, int in, int out, i
   }
 }
 
-// ------------------------------------------------------------ block check rounds
-// One round of the online check (Sec. 3) by a block of 8 warps: 32 consecutive
-// entries, entry e = base + lane.  Warp w is lane w of the canonical sum: it loads the
-// partials k = w, w+8, ... of its lane's entry (coalesced across the warp) and one
-// interpolation input (w = 0..4 the entry and its neighbours, 5 the constant-term
-// checksum, 6/7 the boundary-term values).  finish() meets the eight warp sums in
-// shared memory and warp 0 adds them in order, interpolates and tests.  load()
-// before a sweep and finish() after it hide the load latency.  The arithmetic is that
-// of sum_partials and predict_a/b, so results are bit-identical to check_entry.
-struct CheckShared {
-  float th[kLanes][32], tl[kLanes][32];
-  double td[kLanes][32];
-  double p[kLanes][32];
+// ------------------------------------------------------------ warp check
+// The interpolation weights of Theorem 1 in FP64, converted once per thread (the
+// float-to-double conversions are exact, so this equals converting per entry).
+struct InterpW {
+  double a0, b0, cw, ce, cn, cs, cb, ct;
+  __device__ __forceinline__ explicit InterpW(const Coef& k)
+      : a0(weight_sum3(k.cc, k.cn, k.cs)), b0(weight_sum3(k.cc, k.cw, k.ce)), cw(k.cw), ce(k.ce), cn(k.cn),
+        cs(k.cs), cb(k.cb), ct(k.ct) {}
 };
 
+// One entry of the online check (Sec. 3), e < nz*nx addressing a[z][x] and the rest
+// b[z][y]: the entry's tile partials summed in the canonical order (lanes j = k mod 8,
+// combined in order), the interpolation from a^t / b^t (Theorem 1), the test of Sec.
+// 3.4, the entry appended to its plane's list if it fails.  The partial loads are
+// issued eight at a time; across a warp (32 consecutive entries) every load is
+// coalesced.  Arithmetic identical to check_entry and to the persistent kernel's
+// check warp.
 template <int ACC>
-struct CheckRound {
-  static constexpr int PF = 8;  // prefetched partials per warp lane (more are loaded in finish)
-  typename PartialType<ACC>::T pv[PF];
-  double pin;
-  int e;  // this thread's entry, -1 if beyond the range
-
-  // where entry e's partials live
-  __device__ __forceinline__ static void partials_of(const GridDev& g, int e, int pbuf, const void** P, size_t* i0,
-                                                     size_t* stride, int* n) {
-    const int na = g.nz * g.nx;
-    if (e < na) {
-      const int z = e / g.nx, x = e - z * g.nx;
-      *P = pbuf ? g.PA2 : g.PA;
-      *i0 = (size_t)z * g.pa_stride + x;
-      *stride = (size_t)g.nz * g.pa_stride;
-      *n = g.nty;
-    } else {
-      const int b = e - na;
-      const int z = b / g.ny, y = b - z * g.ny;
-      *P = pbuf ? g.PB2 : g.PB;
-      *i0 = (size_t)z * g.pb_stride + y;
-      *stride = (size_t)g.nz * g.pb_stride;
-      *n = g.ntx;
-    }
-  }
-
-  __device__ __forceinline__ void load(const GridDev& g, int in, int pbuf, int base, int end) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    e = base + lane < end ? base + lane : -1;
-    pin = 0.0;
-    if (e < 0) return;
-    const int na = g.nz * g.nx;
-    if (e < na) {
-      const int z = e / g.nx, x = e - z * g.nx;
-      const int xm = x > 0 ? x - 1 : 0, xp = x < g.nx - 1 ? x + 1 : g.nx - 1;
-      const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
-      const double* A = g.A[in];
+__device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, int in, int out, int e) {
+  const int na = g.nz * g.nx;
+  const Coef& k = g.k;
+  double c, v0, v1, v2, v3, v4, edge = 0.0;
+  const void* P;
+  size_t i0, stride;
+  int np, z, idx, which;
+  if (e < na) {
+    z = e / g.nx;
+    idx = e - z * g.nx;
+    which = 0;
+    const int x = idx, nx = g.nx;
+    const int xm = x > 0 ? x - 1 : 0, xp = x < nx - 1 ? x + 1 : nx - 1;
+    const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+    const double* A = g.A[in];
+    c = g.cx[(size_t)z * nx + x];
+    v0 = __ldcg(A + (size_t)z * nx + x);
+    v1 = __ldcg(A + (size_t)z * nx + xm);
+    v2 = __ldcg(A + (size_t)z * nx + xp);
+    v3 = __ldcg(A + (size_t)zm * nx + x);
+    v4 = __ldcg(A + (size_t)zp * nx + x);
+    if (k.cn != k.cs) {
       const size_t pl = (size_t)z * g.ny * g.px;
-      switch (w) {
-        case 0: pin = __ldcg(A + (size_t)z * g.nx + x); break;
-        case 1: pin = __ldcg(A + (size_t)z * g.nx + xm); break;
-        case 2: pin = __ldcg(A + (size_t)z * g.nx + xp); break;
-        case 3: pin = __ldcg(A + (size_t)zm * g.nx + x); break;
-        case 4: pin = __ldcg(A + (size_t)zp * g.nx + x); break;
-        case 5: pin = g.cx[(size_t)z * g.nx + x]; break;
-        case 6: if (g.k.cn != g.k.cs) pin = (double)__ldcg(g.u[in] + pl + x); break;
-        default: if (g.k.cn != g.k.cs) pin = (double)__ldcg(g.u[in] + pl + (size_t)(g.ny - 1) * g.px + x); break;
-      }
-    } else {
-      const int b = e - na;
-      const int z = b / g.ny, y = b - z * g.ny;
-      const int ym = y > 0 ? y - 1 : 0, yp = y < g.ny - 1 ? y + 1 : g.ny - 1;
-      const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
-      const double* B = g.B[in];
+      edge = edge_term(k.cn, k.cs, __ldcg(g.u[in] + pl + x), __ldcg(g.u[in] + pl + (size_t)(g.ny - 1) * g.px + x));
+    }
+    P = g.PA;
+    i0 = (size_t)z * g.pa_stride + x;
+    stride = (size_t)g.nz * g.pa_stride;
+    np = g.nty;
+  } else {
+    const int b = e - na;
+    z = b / g.ny;
+    idx = b - z * g.ny;
+    which = 1;
+    const int y = idx, ny = g.ny;
+    const int ym = y > 0 ? y - 1 : 0, yp = y < ny - 1 ? y + 1 : ny - 1;
+    const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+    const double* B = g.B[in];
+    c = g.cy[(size_t)z * ny + y];
+    v0 = __ldcg(B + (size_t)z * ny + y);
+    v1 = __ldcg(B + (size_t)z * ny + ym);
+    v2 = __ldcg(B + (size_t)z * ny + yp);
+    v3 = __ldcg(B + (size_t)zm * ny + y);
+    v4 = __ldcg(B + (size_t)zp * ny + y);
+    if (k.cw != k.ce) {
       const size_t row = ((size_t)z * g.ny + y) * g.px;
-      switch (w) {
-        case 0: pin = __ldcg(B + (size_t)z * g.ny + y); break;
-        case 1: pin = __ldcg(B + (size_t)z * g.ny + ym); break;
-        case 2: pin = __ldcg(B + (size_t)z * g.ny + yp); break;
-        case 3: pin = __ldcg(B + (size_t)zm * g.ny + y); break;
-        case 4: pin = __ldcg(B + (size_t)zp * g.ny + y); break;
-        case 5: pin = g.cy[(size_t)z * g.ny + y]; break;
-        case 6: if (g.k.cw != g.k.ce) pin = (double)__ldcg(g.u[in] + row); break;
-        default: if (g.k.cw != g.k.ce) pin = (double)__ldcg(g.u[in] + row + g.nx - 1); break;
-      }
+      edge = edge_term(k.cw, k.ce, __ldcg(g.u[in] + row), __ldcg(g.u[in] + row + g.nx - 1));
     }
-    const void* P;
-    size_t i0, stride;
-    int n;
-    partials_of(g, e, pbuf, &P, &i0, &stride, &n);
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      const int k = w + kLanes * q;
-      if (k < n) pv[q] = load_raw<ACC>(P, i0 + (size_t)k * stride);
-    }
+    P = g.PB;
+    i0 = (size_t)z * g.pb_stride + y;
+    stride = (size_t)g.nz * g.pb_stride;
+    np = g.ntx;
   }
-
-  // every thread of the block must call this
-  __device__ __forceinline__ void finish(const GridDev& g, int out, int pbuf, unsigned* any, CheckShared& sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    LaneSum t;
-    if (e >= 0) {
-      const void* P;
-      size_t i0, stride;
-      int n;
-      partials_of(g, e, pbuf, &P, &i0, &stride, &n);
+  using T = typename PartialType<ACC>::T;
+  LaneSum L[kLanes];
+  int q = 0;
+  for (; q + kLanes <= np; q += kLanes) {
+    T v[kLanes];
 #pragma unroll
-      for (int q = 0; q < PF; ++q)
-        if (w + kLanes * q < n) t.add(pv[q]);
-      for (int k = w + kLanes * PF; k < n; k += kLanes) t.add(load_raw<ACC>(P, i0 + (size_t)k * stride));
-    }
-    sh.th[w][lane] = t.hi;
-    sh.tl[w][lane] = t.lo;
-    sh.td[w][lane] = t.d;
-    sh.p[w][lane] = pin;
-    __syncthreads();
-    if (w == 0 && e >= 0) {
-      LaneSum acc;
-      acc.hi = sh.th[0][lane];
-      acc.lo = sh.tl[0][lane];
-      acc.d = sh.td[0][lane];
+    for (int j = 0; j < kLanes; ++j) v[j] = load_raw<ACC>(P, i0 + (size_t)(q + j) * stride);
 #pragma unroll
-      for (int q = 1; q < kLanes; ++q) {
-        LaneSum o;
-        o.hi = sh.th[q][lane];
-        o.lo = sh.tl[q][lane];
-        o.d = sh.td[q][lane];
-        acc.merge<ACC>(o);
-      }
-      const double s = acc.total<ACC>();
-      const double* v = &sh.p[0][lane];
-      const int st = 32;  // stride between the lanes' inputs in sh.p
-      const Coef& k = g.k;
-      const int na = g.nz * g.nx;
-      if (e < na) {
-        const int z = e / g.nx, x = e - z * g.nx;
-        const double edge = k.cn != k.cs ? edge_term(k.cn, k.cs, (float)v[6 * st], (float)v[7 * st]) : 0.0;
-        const double p = interp(v[5 * st], v[0], v[st], v[2 * st], v[3 * st], v[4 * st], weight_sum3(k.cc, k.cn, k.cs),
-                                k.cw, k.ce, k.cb, k.ct, edge);
-        g.A[out][e] = s;
-        g.AP[0][e] = p;
-        if (fails(p, s, g.eps)) append_fail(g, z, 0, x, any);
-        note_resid(g, p, s);
-      } else {
-        const int b = e - na;
-        const int z = b / g.ny, y = b - z * g.ny;
-        const double edge = k.cw != k.ce ? edge_term(k.cw, k.ce, (float)v[6 * st], (float)v[7 * st]) : 0.0;
-        const double p = interp(v[5 * st], v[0], v[st], v[2 * st], v[3 * st], v[4 * st], weight_sum3(k.cc, k.cw, k.ce),
-                                k.cn, k.cs, k.cb, k.ct, edge);
-        g.B[out][b] = s;
-        g.BP[0][b] = p;
-        if (fails(p, s, g.eps)) append_fail(g, z, 1, y, any);
-        note_resid(g, p, s);
-      }
-    }
-    __syncthreads();
+    for (int j = 0; j < kLanes; ++j) L[j].add(v[j]);
   }
-};
+#pragma unroll
+  for (int j = 0; j < kLanes; ++j)
+    if (q + j < np) L[j].add(load_raw<ACC>(P, i0 + (size_t)(q + j) * stride));
+  LaneSum t = L[0];
+#pragma unroll
+  for (int j = 1; j < kLanes; ++j) t.merge<ACC>(L[j]);
+  const double s = t.total<ACC>();
+  double p;
+  if (which == 0) {
+    p = interp(c, v0, v1, v2, v3, v4, w.a0, w.cw, w.ce, w.cb, w.ct, edge);
+    g.A[out][e] = s;
+    g.AP[0][e] = p;
+  } else {
+    p = interp(c, v0, v1, v2, v3, v4, w.b0, w.cn, w.cs, w.cb, w.ct, edge);
+    g.B[out][e - na] = s;
+    g.BP[0][e - na] = p;
+  }
+  if (fails(p, s, g.eps)) append_fail(g, z, which, idx);
+  note_resid(g, p, s);
+}
 
-// Rounds base0, base0 + stride, ... (below n) of the online check by one block; the
-// loads of the next round are issued before the current round is finished, so one
-// round's memory latency hides behind the other's reduction.
+// Entries of warps wbase, wbase + wstride, ... (32 consecutive entries each, below n)
+// checked by the calling warp; no block-wide synchronisation.
 template <int ACC>
-__device__ __forceinline__ void check_rounds(const GridDev& g, int in, int out, int base0, int stride, int n,
-                                             CheckShared& sh) {
-  CheckRound<ACC> ca, cb;
-  int b = base0;
-  if (b >= n) return;
-  ca.load(g, in, 0, b, n);
-  for (;;) {
-    const int b1 = b + stride;
-    if (b1 < n) cb.load(g, in, 0, b1, n);
-    ca.finish(g, out, 0, nullptr, sh);
-    if (b1 >= n) return;
-    const int b2 = b1 + stride;
-    if (b2 < n) ca.load(g, in, 0, b2, n);
-    cb.finish(g, out, 0, nullptr, sh);
-    if (b2 >= n) return;
-    b = b2;
-  }
+__device__ __forceinline__ void check_warps(const GridDev& g, int in, int out, int wbase, int wstride, int n) {
+  const InterpW w(g.k);
+  const int lane = threadIdx.x & 31;
+  for (int base = wbase * 32; base < n; base += wstride * 32)
+    if (base + lane < n) check_lane<ACC>(g, w, in, out, base + lane);
 }
 
 }  // namespace abft

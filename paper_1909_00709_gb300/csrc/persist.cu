@@ -205,6 +205,19 @@ __device__ __forceinline__ void fix_box(const GridDev& g, int4 f, int lo[3], int
   else { lo[2] = max(xx - 1, 0); hi[2] = min(xx + 1, g.nx - 1); }
 }
 
+// points of u^{s+1} that repair_next would recompute for the fixes in `sm` (every
+// plane when the fix list overflowed)
+__device__ __forceinline__ long long repair_volume(const GridDev& g, const ResolveSmem& sm) {
+  if (sm.nfix > kFixCap) return (long long)g.nz * g.ny * g.nx;
+  long long v = 0;
+  for (int i = 0; i < sm.nfix; ++i) {
+    int lo[3], hi[3];
+    fix_box(g, sm.fix[i], lo, hi);
+    v += (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+  }
+  return v;
+}
+
 // Block 0: after the fixes `sm.fix` of u^s, recompute the affected points of u^{s+1}
 // (the output of sweep `sweep_s`, whose flips are re-applied) and the partials
 // (buffer PA/PB) of every tile row and column that holds one.
@@ -325,12 +338,25 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         resolve_planes_into(rs, g, g.u[prv], g.u[cur], g.A[cur], g.B[cur], g.AP[0], g.BP[0], s - 1, ctrl, ev,
                             &g.gc->unresolved);
         __syncthreads();
-        if (sweep)
+        // a targeted repair by this block only while it is smaller than a few tiles'
+        // work; beyond that every CTA recomputes its tiles of the speculative sweep
+        const bool redo = sweep && repair_volume(g, rs) > 4LL * TY * kTX * g.nz;
+        if (sweep && !redo)
           repair_next<Tiles, TY, ACC>(g, g.u[cur], g.u[nxt], pb_nxt ? g.PA2 : g.PA, pb_nxt ? g.PB2 : g.PB, rs, s,
                                       ctrl, sched);
+        if (threadIdx.x == 0) g.gc->redo = redo ? 1u : 0u;
         fence_proxy_async_global();
       }
       ok = grid_barrier(bar, ctrl);
+      if (ok && sweep && ld_acquire_u32(&g.gc->redo) != 0) {
+        if (sweeper)
+          for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, !resident_c);
+            tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl,
+                                          pb_nxt);
+          }
+        ok = grid_barrier(bar, ctrl);
+      }
     }
   }
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;

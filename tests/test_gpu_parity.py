@@ -147,6 +147,31 @@ def test_persistent_and_per_launch_paths_agree_bitwise(abi, mode, shallow, shape
     assert out[0][1] == out[1][1]
 
 
+@pytest.mark.parametrize("shape,rate", [((300, 130, 40), 100.0), ((200, 150, 12), 60.0)])
+def test_persistent_heavy_flips_recompute_the_speculative_sweep(abi, orc, shape, rate):
+    """So many failures in one sweep that repairing the speculative next state point by
+    point would exceed a few tiles' work: every CTA recomputes its tiles instead.  The
+    result must equal the per-launch path bit for bit and find the oracle's events."""
+    steps = 12
+    sched = orc.schedule(21, rate, 0xFFFFFFFF, shape, 0, steps)
+    assert len(sched) > 400
+    out = []
+    for persistent in (0, 1):
+        with gpu_context(abi, [shape], [13], persistent=persistent, max_flips_per_step=128) as ctx:
+            ctx.inject(21, rate, 0xFFFFFFFF)
+            ctx.step(steps, ONLINE)
+            out.append((ctx.read(0), sorted(map(tuple, ctx.events()[["step", "z", "y", "x", "kind"]].tolist()))))
+    np.testing.assert_array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert out[0][1] == out[1][1]
+    ref = oracle_run(orc, shape, 13, steps, orc.MODE_ONLINE, sched)
+    marg = ref["marginal"]
+    got = {(k[0], k[1], k[2], k[3], k[4]) for k in out[1][1] if (k[0], k[1]) not in marg}
+    exp = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"])) for e in ref["events"]
+           if (int(e["step"]), int(e["z"])) not in marg}
+    assert got == exp
+    assert rel_err(out[1][0], ref["u"]) < value_tol(steps)
+
+
 FIXUP_CASES = {
     # flips in consecutive sweeps at neighbouring points: when sweep 5's flip is
     # corrected, the repaired output of sweep 6 must still carry sweep 6's flip
