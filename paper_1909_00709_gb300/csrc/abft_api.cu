@@ -100,7 +100,7 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
   P->flips = b.take(sizeof(DevFlip) * P->sched_cap);
   P->off = b.take(sizeof(int) * (kSchedSteps + 1));
   P->bgrid = b.take(sizeof(GridDev) * n);
-  P->btmap = b.take(sizeof(CUtensorMap) * 4 * n);
+  P->btmap = b.take(sizeof(CUtensorMap) * kBatchMaps * n);
   P->broles = b.take(sizeof(BatchRole) * n);
   P->bints = b.take(sizeof(int) * (4 * (size_t)n + 16));
   P->total = align_up(b.off, 256);
@@ -275,6 +275,7 @@ struct abft_ctx {
   // batched launches (contexts with several grids)
   struct BClass {
     int shallow, ty, smem, blocks, n, grids_at, off_at;
+    int box, nw;  // check launch: box bytes (0: no TMA boxes), warps per block
   };
   std::vector<BClass> bcls;      // sweep launches, one per tile class
   BClass bchk{};                 // the check launch
@@ -515,7 +516,8 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
     if (mode == ABFT_MODE_ONLINE) {
       const int out = (in + 1) % 3;  // the verified state moves with every sweep
       CK(run(ctx, kKSweepProt, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
-      CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(L, g, in, out); }));
+      const PartialMaps* pm = reinterpret_cast<const PartialMaps*>(&ctx->tm_p[4 * gi]);
+      CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(L, g, *pm, in, out); }));
       CK(run(ctx, kKOther, [&] { return launch_resolve(L, g, in, out); }));
       ctx->cur[gi] = out;
       ctx->ref[gi] = out;
@@ -533,13 +535,15 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
 }
 
 // Work lists of the batched launches: grids grouped by tile class, deepest first;
-// the check launch takes one block per kBatchRounds rounds of 32 entries of a grid.
+// the check launch gives each grid blocks of 32-entry rounds (eight per warp with TMA
+// boxes, kBatchRounds per block otherwise).
 void build_batch_tables(abft_ctx* ctx) {
   const int n = ctx->n;
-  ctx->h_btmap.resize(4 * (size_t)n);
+  ctx->h_btmap.resize((size_t)kBatchMaps * n);
   for (int i = 0; i < n; ++i) {
-    for (int k = 0; k < 3; ++k) ctx->h_btmap[4 * i + k] = ctx->tm_u[3 * i + k];
-    ctx->h_btmap[4 * i + 3] = ctx->tm_c[i];
+    for (int k = 0; k < 3; ++k) ctx->h_btmap[kBatchMaps * i + k] = ctx->tm_u[3 * i + k];
+    ctx->h_btmap[kBatchMaps * i + 3] = ctx->tm_c[i];
+    for (int k = 0; k < 4; ++k) ctx->h_btmap[kBatchMaps * i + 4 + k] = ctx->tm_p[4 * i + k];
   }
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -578,12 +582,26 @@ void build_batch_tables(abft_ctx* ctx) {
   abft_ctx::BClass& k = ctx->bchk;
   k = abft_ctx::BClass{};
   k.grids_at = (int)grids.size();
+  // the check reads the partials with plain coalesced loads: measured on the uneven
+  // 256-grid batch, per-warp TMA boxes (one descriptor per grid, fetched from global
+  // memory) were slower; the single-grid check uses boxes
+  bool box = false;
+  int box_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    box = box && check_box_usable(ctx->g[i]);  // (kept for a future per-shape choice)
+    box_bytes = std::max(box_bytes, (check_box_bytes_host(ctx->g[i].nty, ctx->g[i].ntx, ctx->opt.acc) + 127) / 128 * 128);
+  }
+  k.box = box ? box_bytes : 0;
+  k.nw = box ? check_box_warps(box_bytes) : 8;
+  k.smem = box ? 256 + k.nw * box_bytes : 0;
+  const int per_block = box ? 8 * k.nw : kBatchRounds;  // 32-entry rounds per block
   std::vector<int> koff{0};
   for (int i = 0; i < n; ++i) {
     const GridDev& g = ctx->g[i];
     grids.push_back(i);
-    const int64_t rounds = ((int64_t)g.nz * (g.nx + g.ny) + 31) / 32;
-    koff.push_back(koff.back() + (int)((rounds + kBatchRounds - 1) / kBatchRounds));
+    const int64_t rounds = box ? (int64_t)g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox)
+                               : ((int64_t)g.nz * (g.nx + g.ny) + 31) / 32;
+    koff.push_back(koff.back() + (int)((rounds + per_block - 1) / per_block));
   }
   k.n = n;
   k.blocks = koff.back();
@@ -625,7 +643,7 @@ cudaError_t batch_sweep(abft_ctx* ctx, const Launch& L, bool prot, bool counted)
   }
   if (!prot) return cudaSuccess;
   const BatchArgs a = batch_args(ctx, ctx->bchk);
-  auto f = [&] { return launch_check_batch(L, a, ctx->bchk.blocks, acc); };
+  auto f = [&] { return launch_check_batch(L, a, ctx->bchk.blocks, acc, ctx->bchk.box, ctx->bchk.nw, ctx->bchk.smem); };
   return counted ? run(ctx, kKCheckOnline, f) : f();
 }
 
@@ -661,6 +679,7 @@ abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
       if (s) return s;
     }
   for (const auto& b : ctx->bcls) CK(batch_prepare(b.shallow, b.ty, prot, ctx->opt.acc, b.smem));
+  if (prot && ctx->bchk.box) CK(batch_check_prepare(ctx->opt.acc, ctx->bchk.smem));
   if (ctx->roles_pending) CK(cudaEventSynchronize(ctx->roles_ev));  // the previous upload has been read
   for (int gi = 0; gi < ctx->n; ++gi) {
     BatchRole& r = ctx->h_roles[gi];

@@ -125,7 +125,15 @@ cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& t
                          const CUtensorMap& tm_c, int in, int out, bool prot);
 cudaError_t launch_source_term(const Launch& L, const GridDev& g, const abft_coeffs& co);
 cudaError_t launch_checksums(const Launch& L, const GridDev& g, const float* u, double* A, double* B);
-cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out);
+// the tensor maps of a grid's partial buffers PA, PA2, PB, PB2 (make_partial_maps)
+struct PartialMaps {
+  CUtensorMap m[4];
+};
+cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out);
+// the box check needs at most 256 tiles along x and along y
+bool check_box_usable(const GridDev& g);
+int check_box_bytes_host(int nty, int ntx, int acc);
+int check_box_warps(int box_bytes);
 // location and correction after launch_check_online, one block per plane
 cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out);
 cudaError_t launch_reduce_partials(const Launch& L, const GridDev& g, int out);
@@ -157,9 +165,10 @@ struct BatchRole {
 
 // one batched launch: the blocks of `n` grids, grid grids[i] owning blocks
 // off[i] .. off[i+1]-1 (all arrays in device memory)
+constexpr int kBatchMaps = 8;  // tensor maps per grid: u[0], u[1], u[2], C, PA, PA2, PB, PB2
 struct BatchArgs {
   const GridDev* g;          // [n_grids]
-  const CUtensorMap* tm;     // [n_grids][4]: u[0], u[1], u[2], C
+  const CUtensorMap* tm;     // [n_grids][kBatchMaps]
   const BatchRole* roles;    // [n_grids]
   const int* grids;
   const int* off;            // [n + 1]
@@ -170,6 +179,9 @@ int batch_sweep_smem(int shallow, int ty, int nz);
 cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int smem);
 cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, int smem, int shallow, int ty,
                                bool prot, int acc);
-cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc);
+// box > 0: the partials come in TMA boxes of `box` bytes, nw warps per block, `smem`
+// bytes of dynamic shared memory; box == 0: plain loads, 8 warps per block
+cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc, int box, int nw, int smem);
+cudaError_t batch_check_prepare(int acc, int smem);
 
 }  // namespace abft

@@ -20,8 +20,6 @@
 
 namespace abft {
 
-constexpr int kBatchCheckThreads = 256;
-
 __device__ __forceinline__ int batch_slot(const int* __restrict__ off, int n, int b) {
   int lo = 0, hi = n;  // off[lo] <= b < off[hi]
   while (hi - lo > 1) {
@@ -67,8 +65,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
   const long long step = g.gc->step;
   int in, out;
   batch_roles(a.roles[gi], step, &in, &out);
-  const CUtensorMap* tm_u = a.tm + 4 * gi + in;
-  const CUtensorMap* tm_c = a.tm + 4 * gi + 3;
+  const CUtensorMap* tm_u = a.tm + kBatchMaps * gi + in;
+  const CUtensorMap* tm_c = a.tm + kBatchMaps * gi + 3;
   float* uout = pick3(g.u[0], g.u[1], g.u[2], out);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
@@ -94,15 +92,18 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
 }
 
 // The online check of the sweep just done (Sec. 3) for every grid of the batch:
-// each block's warps take rounds of 32 entries of one grid (kBatchRounds per block);
-// that grid's last block to finish locates and corrects (Sec. 3.5).
-template <int ACC>
-__global__ void __launch_bounds__(kBatchCheckThreads)
-    k_check_batch(const BatchArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev) {
+// each block's warps take 32-entry rounds of one grid (BOX: one TMA box of all tiles'
+// partials per round and warp; otherwise plain coalesced loads); that grid's last
+// block to finish locates and corrects (Sec. 3.5).
+template <int ACC, bool BOX>
+__global__ void __launch_bounds__(256)
+    k_check_batch(const BatchArgs a, int box, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int slot = batch_slot(a.off, a.n, blockIdx.x);
   const int gi = __ldg(a.grids + slot);
   const int b0 = __ldg(a.off + slot);
   const int lb = blockIdx.x - b0, nb = __ldg(a.off + slot + 1) - b0;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the grid's descriptor, its buffer roles normalised to slots 0 (the state the sweep
   // read) and 1 (its result) so that every index into its arrays is a constant; kept
   // in shared memory, where the location step can take its address
@@ -128,9 +129,27 @@ __global__ void __launch_bounds__(kBatchCheckThreads)
   __syncthreads();
   const GridDev& g = sg;
   const long long s = s_step;
-  const int n = g.nz * (g.nx + g.ny);
-  const int nw = kBatchCheckThreads / 32;
-  check_warps<ACC>(g, 0, 1, lb * nw + (int)(threadIdx.x >> 5), nb * nw, n);
+  if (BOX) {
+    const CUtensorMap* tm_p = a.tm + kBatchMaps * gi + 4;
+    unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base) + warp;  // at most 8 warps
+    unsigned char* buf = base + 128 + (size_t)warp * box;
+    if (lane == 0) {
+      tensormap_acquire(tm_p);
+      tensormap_acquire(tm_p + 2);
+      prefetch_tensormap(tm_p);
+      prefetch_tensormap(tm_p + 2);
+      mbar_init(bar, 1);
+      fence_barrier_init();
+    }
+    __syncwarp();
+    unsigned phase = 0;
+    const int rounds = check_rounds_of(g);
+    for (int r = lb * nw + warp; r < rounds; r += nb * nw)
+      check_box_round<ACC>(g, tm_p, 0, 1, 0, r, buf, bar, phase, ctrl, nullptr);
+  } else {
+    check_warps<ACC>(g, 0, 1, lb * nw + warp, nb * nw, g.nz * (g.nx + g.ny));
+  }
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
@@ -205,14 +224,33 @@ cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, 
   return dispatch(false, &L, &a, blocks, smem, shallow, ty, prot, acc);
 }
 
-cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc) {
+template <int ACC>
+static cudaError_t check_batch_t(const Launch& L, const BatchArgs& a, int blocks, int box, int nw, int smem) {
+  if (box > 0)
+    k_check_batch<ACC, true><<<blocks, nw * 32, smem, L.s>>>(a, box, L.ctrl, L.events);
+  else
+    k_check_batch<ACC, false><<<blocks, 256, 0, L.s>>>(a, 0, L.ctrl, L.events);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_check_prepare(int acc, int smem) {
+  switch (acc) {
+    case ABFT_ACC_TWOSUM:
+      return cudaFuncSetAttribute(k_check_batch<ABFT_ACC_TWOSUM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    case ABFT_ACC_FP64:
+      return cudaFuncSetAttribute(k_check_batch<ABFT_ACC_FP64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    default:
+      return cudaFuncSetAttribute(k_check_batch<ABFT_ACC_FP32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
+}
+
+cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc, int box, int nw, int smem) {
   if (blocks <= 0) return cudaSuccess;
   switch (acc) {
-    case ABFT_ACC_TWOSUM: k_check_batch<ABFT_ACC_TWOSUM><<<blocks, kBatchCheckThreads, 0, L.s>>>(a, L.ctrl, L.events); break;
-    case ABFT_ACC_FP64: k_check_batch<ABFT_ACC_FP64><<<blocks, kBatchCheckThreads, 0, L.s>>>(a, L.ctrl, L.events); break;
-    default: k_check_batch<ABFT_ACC_FP32><<<blocks, kBatchCheckThreads, 0, L.s>>>(a, L.ctrl, L.events); break;
+    case ABFT_ACC_TWOSUM: return check_batch_t<ABFT_ACC_TWOSUM>(L, a, blocks, box, nw, smem);
+    case ABFT_ACC_FP64: return check_batch_t<ABFT_ACC_FP64>(L, a, blocks, box, nw, smem);
+    default: return check_batch_t<ABFT_ACC_FP32>(L, a, blocks, box, nw, smem);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace abft

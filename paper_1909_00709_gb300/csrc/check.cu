@@ -26,6 +26,31 @@ __global__ void __launch_bounds__(kCheckThreads)
   check_warps<ACC>(g, in, out, blockIdx.x * nw + (int)(threadIdx.x >> 5), gridDim.x * nw, n);
 }
 
+// The same check with the partials brought in by TMA: warp w of a block takes rounds
+// of 32 entries, one box of all tiles' partials per round in its own shared-memory
+// buffer (grids with at most 256 tiles along x and along y).
+template <int ACC>
+__global__ void __launch_bounds__(256)
+    k_check_box(const GridDev g, const __grid_constant__ PartialMaps pm, int in, int out, DevCtrl* ctrl) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int box = (check_box_bytes(g.nty, g.ntx, ACC) + 127) / 128 * 128;
+  unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base) + warp;  // at most 8 warps: 64 bytes of the 128-byte head
+  unsigned char* buf = base + 128 + (size_t)warp * box;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&pm.m[0]);
+    prefetch_tensormap(&pm.m[2]);
+  }
+  __syncwarp();
+  unsigned phase = 0;
+  const int rounds = check_rounds_of(g);
+  for (int r = blockIdx.x * nw + warp; r < rounds; r += gridDim.x * nw)
+    check_box_round<ACC>(g, pm.m, in, out, 0, r, buf, bar, phase, ctrl, nullptr);
+}
+
 // Location and correction (Sec. 3.5) after the online check of the sweep just done,
 // one block per plane with failing entries (planes are independent): a single
 // intersection by Eq. (8), other patterns by recomputing lines from u[in].
@@ -174,7 +199,40 @@ static int sm_count() {
   return cache[dev];
 }
 
-cudaError_t launch_check_online(const Launch& L, const GridDev& g, int in, int out) {
+int check_box_warps(int box_bytes) {
+  const int nw = 65536 / (box_bytes + 128);
+  return nw < 1 ? 1 : (nw > 8 ? 8 : nw);
+}
+
+bool check_box_usable(const GridDev& g) { return g.nty <= 256 && g.ntx <= 256; }
+
+int check_box_bytes_host(int nty, int ntx, int acc) { return check_box_bytes(nty, ntx, acc); }
+
+cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out) {
+  if (check_box_usable(g)) {
+    const int box = (check_box_bytes(g.nty, g.ntx, g.acc) + 127) / 128 * 128;
+    const int nw = check_box_warps(box);
+    const int smem = 256 + nw * box;
+    const long long rounds = (long long)g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
+    const int blocks = (int)std::min<long long>((rounds + nw - 1) / nw, 4LL * sm_count());
+    cudaError_t e = cudaSuccess;
+    switch (g.acc) {
+      case ABFT_ACC_TWOSUM:
+        e = cudaFuncSetAttribute(k_check_box<ABFT_ACC_TWOSUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) k_check_box<ABFT_ACC_TWOSUM><<<blocks, nw * 32, smem, L.s>>>(g, pm, in, out, L.ctrl);
+        break;
+      case ABFT_ACC_FP64:
+        e = cudaFuncSetAttribute(k_check_box<ABFT_ACC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) k_check_box<ABFT_ACC_FP64><<<blocks, nw * 32, smem, L.s>>>(g, pm, in, out, L.ctrl);
+        break;
+      default:
+        e = cudaFuncSetAttribute(k_check_box<ABFT_ACC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) k_check_box<ABFT_ACC_FP32><<<blocks, nw * 32, smem, L.s>>>(g, pm, in, out, L.ctrl);
+        break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   // 32 entries per warp, up to one wave of 8 blocks per SM; further entries by striding
   const int blocks =
       (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + kCheckThreads - 1) / kCheckThreads, 8LL * sm_count());

@@ -75,110 +75,6 @@ __global__ void __launch_bounds__(256, 2)
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
 }
 
-// ------------------------------------------------------------ check warp
-// The online kernel's check warp.  Entries are taken in rounds of 32 consecutive
-// entries of one plane (a[z][32 xb ...] or b[z][32 yb ...]); one TMA box brings all
-// tiles' partials of a round into shared memory (its own mbarrier), while each lane
-// loads its entry's interpolation inputs.  The lane then sums its entry's partials in
-// the canonical order (sum_partials) and tests as check_entry does, so the results
-// are bit-identical to the other paths.  Runs concurrently with the sweep warps and
-// takes no block-wide barrier.
-template <int ACC>
-__device__ __forceinline__ void check_warp_round(const PersistArgs& a, const GridDev& g, int in, int out, int pbuf,
-                                                 int round, unsigned char* buf, uint64_t* cbar, unsigned& phase,
-                                                 DevCtrl* ctrl, unsigned* any) {
-  using T = typename PartialType<ACC>::T;
-  constexpr int per = ACC == ABFT_ACC_TWOSUM ? 2 : 1;
-  const int lane = threadIdx.x & 31;
-  const int nxb = (g.nx + kCheckBox - 1) / kCheckBox;
-  const int ra = g.nz * nxb;
-  const bool is_a = round < ra;
-  int z, c, len, n;
-  const CUtensorMap* tm;
-  if (is_a) {
-    z = round / nxb;
-    c = (round - z * nxb) * kCheckBox;
-    len = g.nx; n = g.nty;
-    tm = &a.tm_p[pbuf];
-  } else {
-    const int nyb = (g.ny + kCheckBox - 1) / kCheckBox;
-    const int r = round - ra;
-    z = r / nyb;
-    c = (r - z * nyb) * kCheckBox;
-    len = g.ny; n = g.ntx;
-    tm = &a.tm_p[2 + pbuf];
-  }
-  if (lane == 0) {
-    fence_proxy_async();  // the previous round's reads of buf come before this TMA write
-    mbar_expect_tx(cbar, kCheckBox * per * (ACC == ABFT_ACC_FP64 ? 8 : 4) * n);
-    tma_load_3d(buf, tm, c * per, z, 0, cbar);
-  }
-  const int idx = c + lane;
-  const bool live = idx < len;
-  // interpolation inputs while the box is in flight
-  const int im = idx > 0 ? idx - 1 : 0, ip = idx < len - 1 ? idx + 1 : len - 1;
-  const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
-  const double* V = is_a ? g.A[in] : g.B[in];
-  const double* CC = is_a ? g.cx : g.cy;
-  const Coef& k = g.k;
-  const bool asym = is_a ? k.cn != k.cs : k.cw != k.ce;
-  double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, cc = 0;
-  float ef = 0.f, el = 0.f;
-  if (live) {
-    v0 = __ldcg(V + (size_t)z * len + idx);
-    v1 = __ldcg(V + (size_t)z * len + im);
-    v2 = __ldcg(V + (size_t)z * len + ip);
-    v3 = __ldcg(V + (size_t)zm * len + idx);
-    v4 = __ldcg(V + (size_t)zp * len + idx);
-    cc = CC[(size_t)z * len + idx];
-    if (asym) {
-      const float* u = g.u[in];
-      if (is_a) {
-        const size_t pl = (size_t)z * g.ny * g.px;
-        ef = __ldcg(u + pl + idx);
-        el = __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + idx);
-      } else {
-        const size_t row = ((size_t)z * g.ny + idx) * g.px;
-        ef = __ldcg(u + row);
-        el = __ldcg(u + row + g.nx - 1);
-      }
-    }
-  }
-  mbar_wait(cbar, phase, ctrl);
-  phase ^= 1u;
-  const T* part = reinterpret_cast<const T*>(buf);
-  LaneSum t[kLanes];
-  if (live) {
-    int q = 0;
-    for (; q + kLanes <= n; q += kLanes) {
-#pragma unroll
-      for (int j = 0; j < kLanes; ++j) t[j].add(part[(q + j) * kCheckBox + lane]);
-    }
-#pragma unroll
-    for (int j = 0; j < kLanes; ++j)
-      if (q + j < n) t[j].add(part[(q + j) * kCheckBox + lane]);
-  }
-  __syncwarp();
-  if (!live) return;
-#pragma unroll
-  for (int j = 1; j < kLanes; ++j) t[0].merge<ACC>(t[j]);
-  const double s = t[0].total<ACC>();
-  double p;
-  if (is_a) {
-    const double edge = asym ? edge_term(k.cn, k.cs, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cn, k.cs), k.cw, k.ce, k.cb, k.ct, edge);
-    g.A[out][(size_t)z * len + idx] = s;
-    g.AP[0][(size_t)z * len + idx] = p;
-  } else {
-    const double edge = asym ? edge_term(k.cw, k.ce, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cw, k.ce), k.cn, k.cs, k.cb, k.ct, edge);
-    g.B[out][(size_t)z * len + idx] = s;
-    g.BP[0][(size_t)z * len + idx] = p;
-  }
-  if (fails(p, s, g.eps)) append_fail(g, z, is_a ? 0 : 1, idx, any);
-  note_resid(g, p, s);
-}
-
 // flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
 __device__ __forceinline__ float reapply_flips(float v, const GridDev& g, DevCtrl* ctrl, const DevSched& sched,
                                                long long step, int z, int y, int x) {
@@ -327,7 +223,7 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         }
     } else if (check) {
       // check warp, concurrently: u^s against the interpolation from a^{s-1}, b^{s-1}
-      for (int r = r0; r < r1; ++r) check_warp_round<ACC>(a, g, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, any);
+      for (int r = r0; r < r1; ++r) check_box_round<ACC>(g, a.tm_p, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, any);
     }
     ok = grid_barrier(bar, ctrl);
     if (!ok || !check) continue;
@@ -364,10 +260,7 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
 
 // extra dynamic shared memory of the online kernel's check warp: alignment slack,
 // mbarrier line, one box
-static int check_smem(const GridDev& g, int acc) {
-  const int per = acc == ABFT_ACC_TWOSUM ? 2 : 1, esz = acc == ABFT_ACC_FP64 ? 8 : 4;
-  return 256 + kCheckBox * per * esz * std::max(g.nty, g.ntx);
-}
+static int check_smem(const GridDev& g, int acc) { return 256 + check_box_bytes(g.nty, g.ntx, acc); }
 
 // ---------------------------------------------------------------- offline
 // Windows of d = delta sweeps (the last may be shorter) from a checkpoint ck (Sec. 4):

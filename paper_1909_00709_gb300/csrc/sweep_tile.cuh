@@ -27,6 +27,10 @@ namespace abft {
 constexpr int kSweepThreads = 256;
 __device__ __forceinline__ void tile_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kSweepThreads) : "memory"); }
 
+// row pitch (floats) of the FP32 epilogue's lane partials: 36 keeps the 16-byte
+// loads of eight consecutive rows on distinct banks
+constexpr int kRowPitch = 36;
+
 template <int TY>
 struct SweepCfg {
   static constexpr int NW = 8;                        // warps per CTA
@@ -36,7 +40,10 @@ struct SweepCfg {
   static constexpr int UBOX_AL = (UBOX + 127) / 128 * 128;
   static constexpr int CBOX = TY * kTX * 4;
   static constexpr int STAGE = UBOX_AL + CBOX;        // multiple of 128
-  static constexpr int RED_HALF = NW * kTX * 8;       // one z-parity of the column reduction buffer
+  // one z-parity of the reduction buffer: column partials [NW][kTX] (8-byte sums), or
+  // for FP32 column partials [NW][kTX] then row lane partials [TY][kRowPitch]
+  static constexpr int RED_HALF_A = NW * kTX * 8, RED_HALF_B = NW * kTX * 4 + TY * kRowPitch * 4;
+  static constexpr int RED_HALF = ((RED_HALF_A > RED_HALF_B ? RED_HALF_A : RED_HALF_B) + 127) / 128 * 128;
   static constexpr int RED = 2 * RED_HALF;
   static constexpr int FLIPS = kLocalFlips * 16 + 16;
   static constexpr int SMEM = 128 + 128 + S * STAGE + RED + FLIPS;  // + slack to align the base
@@ -329,6 +336,10 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
   const int nflip = min(*sm.nlf, kLocalFlips);
   const int gx0 = x0 + 4 * lane;
   const int last = g.nx - 1 - gx0;  // element holding x = nx-1, if 0..3
+  const bool full = x0 + kTX <= g.nx && y0 + TY <= g.ny;  // no ragged edge in this tile
+  // FP32 partials: lane partials through shared memory, reduced by one warp per plane
+  constexpr bool SMEM_EPI = ACC == ABFT_ACC_FP32;
+  static_assert(NW * kTX * 4 + TY * kRowPitch * 4 <= Cfg::RED_HALF, "FP32 epilogue buffer");
 
   for (int z = 0; z < nz; ++z) {
     if (z == 0) wait(0);
@@ -337,6 +348,8 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
     const float* Ub = z > 0 ? sm.stage_u((int)((base + z - 1) % S)) : Uc;
     const float* Ut = z + 1 < nz ? sm.stage_u((int)((base + z + 1) % S)) : Uc;
     const float* Cs = sm.stage_c((int)((base + z) % S));
+    unsigned char* red = sm.red + (z & 1) * Cfg::RED_HALF;
+    float* rowp = reinterpret_cast<float*>(red + NW * kTX * 4);  // FP32 epilogue: [TY][kRowPitch] lane partials
     AccA<ACC> acc;
     if (PROT) acc.zero();
     typename RowPart<ACC>::T rp[Cfg::RPW > 1 ? Cfg::RPW : 2];
@@ -393,13 +406,14 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       if (PROT) {
         float m[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
-        if (Cfg::RPW == 1) AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
+        for (int i = 0; i < 4; ++i) m[i] = full ? v[i] : ((yv && i <= last) ? v[i] : 0.f);
+        if (SMEM_EPI) rowp[r * kRowPitch + lane] = ((m[0] + m[1]) + m[2]) + m[3];  // RowPart<FP32>::of
+        else if (Cfg::RPW == 1) AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
         else rp[rr] = RowPart<ACC>::of(m);
         acc.add(m);
       }
     }
-    if (PROT && Cfg::RPW > 1) {  // this warp's rows reduced together; lane (rr << SH) holds row rr
+    if (PROT && !SMEM_EPI && Cfg::RPW > 1) {  // this warp's rows reduced together; lane (rr << SH) holds row rr
       constexpr int SH = Cfg::RPW == 2 ? 4 : (Cfg::RPW == 4 ? 3 : 2);
       const typename RowPart<ACC>::T tot = reduce_rows<ACC, (Cfg::RPW > 1 ? Cfg::RPW : 2)>(rp, lane);
       const int y = y0 + warp + (lane >> SH) * NW;
@@ -412,9 +426,37 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       fence_proxy_async();
       issue(z - 1 + S);
     }
-    if (PROT && tid < kTX)
+    if (PROT && SMEM_EPI) {
+      // one warp per plane (rotating) reduces the plane's partials: four columns per
+      // lane over the eight warps in order, and row `lane` over its 32 lane partials
+      // by the butterfly's own pairing (the same sums as row_store, bit for bit)
+      if (warp == (z & (NW - 1))) {
+        const float* r = reinterpret_cast<const float*>(red);
+        float4 c = reinterpret_cast<const float4*>(r)[lane];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+          const float4 q = reinterpret_cast<const float4*>(r + w * kTX)[lane];
+          c.x += q.x; c.y += q.y; c.z += q.z; c.w += q.w;
+        }
+        *reinterpret_cast<float4*>(static_cast<float*>(PA) + ((size_t)tyi * nz + z) * g.pa_stride + x0 + 4 * lane) = c;
+        if (lane < TY && y0 + lane < g.ny) {
+          float t[32];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 q = reinterpret_cast<const float4*>(rowp + lane * kRowPitch)[k];
+            t[4 * k] = q.x; t[4 * k + 1] = q.y; t[4 * k + 2] = q.z; t[4 * k + 3] = q.w;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int l = 0; l < o; ++l) t[l] = t[l] + t[l + o];
+          static_cast<float*>(PB)[((size_t)txi * nz + z) * g.pb_stride + y0 + lane] = t[0];
+        }
+      }
+    } else if (PROT && tid < kTX) {
       AccA<ACC>::template column_store<NW>(sm.red + (z & 1) * Cfg::RED_HALF, tid, PA,
                                            ((size_t)tyi * nz + z) * g.pa_stride + x0 + tid);
+    }
   }
   seq = base + (unsigned)nz;
   fence_proxy_async_global();  // this thread's grid stores, before any later TMA read of them
@@ -585,6 +627,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
   void* PB = pbuf ? g.PB2 : g.PB;
   const int gx0 = x0 + 4 * lane;
   const int last = g.nx - 1 - gx0;
+  const bool full = x0 + kTX <= g.nx && y0 + TY <= g.ny;  // no ragged edge in this tile
   constexpr int PLANE = (TY + 2) * kUW;
   for (int z = warp; z < nz; z += NW) {
     const float* Uz = sm.u + z * PLANE;
@@ -646,7 +689,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
       if (PROT) {
         float m[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) m[i] = (yv && i <= last) ? v[i] : 0.f;
+        for (int i = 0; i < 4; ++i) m[i] = full ? v[i] : ((yv && i <= last) ? v[i] : 0.f);
         rp[r] = RowPart<ACC>::of(m);
         acc.add(m);
       }
