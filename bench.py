@@ -37,10 +37,15 @@ SWEEPS = 1000
 RATE = 1e-3
 BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# DRAM bytes (read + write) of one 200-sweep launch of the dominant kernel, from one ncu
+# capture of this build (the working set stays in L2); None for kernels not captured
+TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 16.99e6 + 0.279e6}
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
 LARGE_SWEEPS = 200
+BATCH_GRIDS = 256  # nx, ny ~ U{64..1024}, nz ~ U{4..64}, seeded
+BATCH_RATE = 0.1   # flips per sweep and grid
 ACC_NAMES = ("fp32", "twosum", "fp64")
 
 
@@ -235,6 +240,7 @@ def run_ours(args, rank, world, local):
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    traffic = TRAFFIC_PER_200_SWEEP_LAUNCH.get(kernel_names.get(dom, dom)) if timed_sweeps == 200 else None
 
     # end to end through the public API with host buffers: upload, 1000 sweeps, read back
     e2e = None
@@ -257,11 +263,8 @@ def run_ours(args, rank, world, local):
                "ms_per_step": wall / args.steps * 1e3}
 
     # slowest rank decides
-    t_tot = torch.tensor([ms_prot], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
-    ms_max = float(t_tot.item())
+    from paper_1909_00709_gb300 import replicas
+    ms_max = replicas.slowest(ms_prot, device=dev)
     value = world * n_points() * SWEEPS * args.steps / (ms_max / 1e3) / 1e9
     if rank != 0:
         return
@@ -286,7 +289,7 @@ def run_ours(args, rank, world, local):
                     "rollbacks": off_cnt["rollbacks"]},
         "events": {"corrected": int((events["kind"] == 1).sum()), "recomputed": int((events["kind"] == 2).sum())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": kernel_names.get(dom, dom),
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),
                      "avg_launch_us": dom_avg_s * 1e6, "sweeps_per_launch": sweeps_per_launch,
                      "us_per_sweep": dom_avg_s * 1e6 / sweeps_per_launch, "peak_source": peak_src,
                      "note": "algorithmic 12 B per point-update; the 24 MB working set is L2-resident"},
@@ -357,7 +360,35 @@ def side_runs(dev, stream, flush):
                              ("offline", abi.MODE_OFFLINE, 0.0), ("online_flips", abi.MODE_ONLINE, lam),
                              ("offline_flips", abi.MODE_OFFLINE, lam)):
         large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511)
-    return {"precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
+    # many uneven grids: batched launches (one sweep launch per tile class, one check
+    # launch per sweep, graphs of 50 sweeps) against the same grids advanced one by one
+    shapes = inputs.batch_shapes(BATCH_GRIDS, seed=3)
+    bt, bp = zip(*[inputs.grid_inputs(*sh, seed=1000 + i) for i, sh in enumerate(shapes)])
+    bc = [inputs.hotspot_coeffs(*sh) for sh in shapes]
+    npts = sum(math.prod(sh) for sh in shapes)
+    batch = {"grids": BATCH_GRIDS, "points": npts, "flip_rate_per_sweep_and_grid": BATCH_RATE}
+    for name, opts, sweeps in (("batched", {"batch": 1}, 200), ("grid_by_grid", {"batch": 0}, 40)):
+        with abi.Context(list(shapes), list(bt), list(bp), bc, device=dev, stream=stream, **opts) as c:
+            res = {}
+            for mode, key in ((abi.MODE_NONE, "unprotected"), (abi.MODE_ONLINE, "online")):
+                if mode == abi.MODE_ONLINE:
+                    c.inject(9, BATCH_RATE, 0xFFFFFFFF)
+                c.step(3, mode)
+                flush.fill_(1)
+                l0 = c.counters()["kernel_launches"]
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c.step(sweeps, mode)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                res[key] = {"glups": npts * sweeps / (ms / 1e3) / 1e9, "ms_per_sweep": ms / sweeps,
+                            "launches_per_sweep": (c.counters()["kernel_launches"] - l0) / sweeps}
+            res["overhead_pct"] = (res["online"]["ms_per_sweep"] / res["unprotected"]["ms_per_sweep"] - 1) * 100
+            batch[name] = res
+    return {"batch": batch,
+            "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
                           "variants": prec},
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,
                       "flip_rate_per_sweep": "1e-6 per point in the *_flips runs", "glups": large,

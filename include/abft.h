@@ -98,6 +98,9 @@ typedef struct {
                                at once); 0: always stream the planes */
   int32_t track_residual;   /* 1: keep the largest relative residual |a'-a|/|a| of the entries
                                that pass (abft_counters.max_residual); costs one atomic per entry */
+  int32_t depth;            /* temporal blocking: unprotected sweeps (mode NONE, and the sweeps of
+                               an offline window before its last) advance `depth` (1..4) sweeps per
+                               pass over the grid where a grid is swept launch by launch; 1 = off */
   int32_t batch;            /* 1: a context with several grids advances them all with one sweep
                                launch per tile class and one check launch per sweep (CUDA graphs
                                of graph_steps sweeps); 0: grid by grid. Offline steps always go

@@ -2,12 +2,12 @@
 
 The compute path is the CUDA library ``libabft.so`` (C ABI in ``include/abft.h``),
 reached through the ctypes binding in ``abi``.  ``inputs`` generates seeded
-synthetic workloads.  Submodules load lazily so that input generation works
+synthetic workloads; ``replicas`` holds the host logic of one process per GPU.  Submodules load lazily so that input generation works
 without a GPU or a built library.
 """
 import importlib
 
-__all__ = ["abi", "inputs", "build"]
+__all__ = ["abi", "inputs", "build", "replicas"]
 
 
 def __getattr__(name):

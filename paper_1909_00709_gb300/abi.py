@@ -42,7 +42,8 @@ class abft_options(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
-                ("track_residual", ct.c_int32), ("batch", ct.c_int32), ("stream", ct.c_void_p)]
+                ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("batch", ct.c_int32),
+                ("stream", ct.c_void_p)]
 
 
 class abft_counters(ct.Structure):

@@ -64,7 +64,8 @@ bool valid_options(const abft_options& o) {
          o.event_capacity >= 1 && o.graph_steps >= 0 && o.max_flips_per_step >= 0 &&
          o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
-         (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1);
+         (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1) &&
+         o.depth >= 1 && o.depth <= 4;
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -195,6 +196,30 @@ cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUte
   return cudaSuccess;
 }
 
+cudaError_t make_tb_maps(const GridDev& g, int k, CUtensorMap tm_u[3], CUtensorMap* tm_c, char* err, size_t errlen) {
+  auto enc = encode_fn();
+  if (!enc) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
+    return cudaErrorNotSupported;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.ny * 4};
+  cuuint32_t ebox[3] = {1, 1, 1};
+  cuuint32_t box[3] = {(cuuint32_t)kUW, (cuuint32_t)(kTbRows + 2 * k), 1u};  // u and C alike
+  for (int i = 0; i < 4; ++i) {
+    CUtensorMap* m = i < 3 ? &tm_u[i] : tm_c;
+    void* base = i < 3 ? (void*)g.u[i] : (void*)g.C;
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, ebox,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      snprintf(err, errlen, "cuTensorMapEncodeTiled (temporal blocking) failed (%d)", (int)r);
+      return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t make_partial_maps(const GridDev& g, CUtensorMap tm[4], char* err, size_t errlen) {
   auto enc = encode_fn();
   if (!enc) {
@@ -239,6 +264,7 @@ struct abft_ctx {
   std::vector<abft_coeffs> co;
   std::vector<GridDev> g;
   std::vector<CUtensorMap> tm_u, tm_c, tm_p;
+  std::vector<CUtensorMap> tm_tb;  // temporal blocking (depth >= 2): u[0..2], C per grid
   std::vector<int> cur, ref;
   std::vector<int64_t> ref_step;
   std::vector<char> ck_valid;
@@ -722,6 +748,22 @@ abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
   return ABFT_OK;
 }
 
+// `depth` unprotected sweeps of every grid, one temporally blocked pass per grid
+abft_status tb_all(abft_ctx* ctx) {
+  const Launch L = launcher(ctx);
+  const int k = ctx->opt.depth;
+  for (int gi = 0; gi < ctx->n; ++gi) {
+    const GridDev& g = ctx->g[gi];
+    const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
+    CK(run(ctx, kKSweepPlain,
+           [&] { return launch_sweep_tb(L, g, ctx->tm_tb[4 * gi + in], ctx->tm_tb[4 * gi + 3], out, k); }));
+    ctx->cur[gi] = out;
+    ctx->ck_valid[gi] = 0;
+  }
+  ctx->step += k;
+  return ABFT_OK;
+}
+
 abft_status status_from_device(abft_ctx* ctx) {
   const unsigned st = ctx->h_ctrl->status;
   ctx->status_seen |= st;
@@ -799,7 +841,20 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   abft_status s = clear_verdicts(ctx);
   if (s) return s;
   auto run_window = [&](const std::vector<int>& which) -> abft_status {
+    const int depth = ctx->opt.depth;
     for (int64_t k = 0; k < d; ++k) {
+      if (depth >= 2 && d - 1 - k >= depth) {  // unprotected sweeps of the window, temporally blocked
+        for (int gi : which) {
+          const GridDev& g = ctx->g[gi];
+          const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
+          CK(run(ctx, kKSweepPlain, [&] {
+            return launch_sweep_tb(L, g, ctx->tm_tb[4 * gi + in], ctx->tm_tb[4 * gi + 3], out, depth);
+          }));
+          ctx->cur[gi] = out;
+        }
+        k += depth - 1;
+        continue;
+      }
       for (int gi : which) {
         const GridDev& g = ctx->g[gi];
         const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
@@ -880,6 +935,7 @@ void abft_default_options(abft_options* o) {
   o->event_capacity = 4096;
   o->graph_steps = 50;
   o->batch = 1;
+  o->depth = 1;
   o->tile_y = 0;
   o->max_flips_per_step = 64;
   o->persistent = 1;
@@ -1034,6 +1090,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   ctx->tm_u.resize(3 * n_grids);
   ctx->tm_c.resize(n_grids);
   ctx->tm_p.resize(4 * n_grids);
+  ctx->tm_tb.resize(4 * n_grids);
   ctx->cur.assign(n_grids, 0);
   ctx->ref.assign(n_grids, 0);
   ctx->ref_step.assign(n_grids, 0);
@@ -1060,7 +1117,9 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[0], g.A[0], g.B[0]); }));
     char e[256];
     if (make_tensor_maps(g, g.ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess ||
-        make_partial_maps(g, &ctx->tm_p[4 * i], e, sizeof e) != cudaSuccess) {
+        make_partial_maps(g, &ctx->tm_p[4 * i], e, sizeof e) != cudaSuccess ||
+        (opt->depth >= 2 &&
+         make_tb_maps(g, opt->depth, &ctx->tm_tb[4 * i], &ctx->tm_tb[4 * i + 3], e, sizeof e) != cudaSuccess)) {
       st = fail(ctx, ABFT_E_CUDA, "%s", e);
       return bail(st);
     }
@@ -1160,6 +1219,12 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
       continue;
     }
     for (int64_t k = 0; k < covered; ++k) {
+      if (mode == ABFT_MODE_NONE && ctx->opt.depth >= 2 && covered - k >= ctx->opt.depth) {
+        s = tb_all(ctx);
+        if (s) return s;
+        k += ctx->opt.depth - 1;
+        continue;
+      }
       if (mode == ABFT_MODE_ONLINE)
         for (int gi = 0; gi < ctx->n; ++gi) {
           s = ensure_checksums(ctx, gi);

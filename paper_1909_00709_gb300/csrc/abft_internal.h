@@ -153,6 +153,13 @@ bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);
 
+// ------------------------------------------------------------ temporal blocking
+// k (2..4) unprotected sweeps in one pass; maps with boxes of 136 columns by 8 + 2k rows
+constexpr int kTbRows = 8;
+cudaError_t make_tb_maps(const GridDev& g, int k, CUtensorMap tm_u[3], CUtensorMap* tm_c, char* err, size_t errlen);
+cudaError_t launch_sweep_tb(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
+                            int out, int k);
+
 // ------------------------------------------------------------ batched grids
 // Buffer roles of sweep s of one grid in a batched run that started at sweep s0.
 // mode 1 (protected): in = (first + s - s0) mod 3, out = in + 1 mod 3.

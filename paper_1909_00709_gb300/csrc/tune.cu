@@ -3,7 +3,8 @@
 // The fastest tiling depends on the grid: shallow grids (nz <= 16) favour
 // whole-column tiles, small ones a persistent launch (one CTA per tile for the whole
 // run), large ones streaming tiles whose row count trades halo traffic against
-// shared memory and occupancy; batches of uneven grids favour the batched launches.
+// shared memory and occupancy, and temporally blocked passes for their unprotected
+// sweeps; batches of uneven grids favour the batched launches.
 // abft_tune times short runs of every distinct candidate on the GPU, through the
 // public calls only, and returns the fastest as an abft_options.  Results are kept
 // per (shapes, mode, accumulation, Delta) for the life of the process, so tuning a
@@ -23,7 +24,7 @@
 namespace {
 
 struct Cand {
-  int tile_y, shallow, persistent, batch;
+  int tile_y, shallow, persistent, batch, depth;
 };
 
 struct Result {
@@ -47,8 +48,8 @@ std::string key_of(const abft_grid* g, int n, const abft_options* o, int mode, i
 }
 
 // the settings a candidate actually changes for these grids (so equivalent candidates
-// are timed once): per grid the tile class, then persistence and batching
-std::string effect_of(const abft_grid* g, int n, const Cand& c) {
+// are timed once): per grid the tile class, then persistence, batching and depth
+std::string effect_of(const abft_grid* g, int n, const Cand& c, int mode) {
   std::string e;
   char b[32];
   for (int i = 0; i < n; ++i) {
@@ -57,23 +58,26 @@ std::string effect_of(const abft_grid* g, int n, const Cand& c) {
     snprintf(b, sizeof b, "%d%d;", sh ? 1 : 0, ty);
     e += b;
   }
-  snprintf(b, sizeof b, "p%db%d", n > 1 && c.batch ? 0 : c.persistent, n > 1 ? c.batch : 0);
+  snprintf(b, sizeof b, "p%db%dd%d", n > 1 && c.batch ? 0 : c.persistent, n > 1 ? c.batch : 0,
+           mode == ABFT_MODE_ONLINE ? 1 : c.depth);
   return e + b;
 }
 
-std::vector<Cand> candidates(const abft_grid* g, int n) {
+// temporal depth only matters for the unprotected sweeps (mode NONE, offline windows)
+std::vector<Cand> candidates(const abft_grid* g, int n, int mode) {
   std::vector<Cand> out;
   std::vector<std::string> seen;
-  for (int batch : {1, 0})
-    for (int persistent : {1, 0})
-      for (int shallow : {1, 0})
-        for (int ty : {8, 16, 32}) {
-          const Cand c{ty, shallow, persistent, batch};
-          const std::string e = effect_of(g, n, c);
-          if (std::find(seen.begin(), seen.end(), e) != seen.end()) continue;
-          seen.push_back(e);
-          out.push_back(c);
-        }
+  for (int depth : {1, 2, 3, 4})
+    for (int batch : {1, 0})
+      for (int persistent : {1, 0})
+        for (int shallow : {1, 0})
+          for (int ty : {8, 16, 32}) {
+            const Cand c{ty, shallow, persistent, batch, depth};
+            const std::string e = effect_of(g, n, c, mode);
+            if (std::find(seen.begin(), seen.end(), e) != seen.end()) continue;
+            seen.push_back(e);
+            out.push_back(c);
+          }
   return out;
 }
 
@@ -83,6 +87,7 @@ abft_options with(const abft_options& base, const Cand& c) {
   o.shallow = c.shallow;
   o.persistent = c.persistent;
   o.batch = c.batch;
+  o.depth = c.depth;
   return o;
 }
 
@@ -92,7 +97,7 @@ extern "C" ABFT_API size_t abft_tune_workspace_bytes(const abft_grid* grids, int
                                                      const abft_options* base) {
   if (!grids || n_grids < 1 || !base) return 0;
   size_t m = 0;
-  for (const Cand& c : candidates(grids, n_grids)) {
+  for (const Cand& c : candidates(grids, n_grids, ABFT_MODE_NONE)) {
     const abft_options o = with(*base, c);
     const size_t b = abft_workspace_bytes(grids, n_grids, &o);
     if (b == 0) return 0;
@@ -127,7 +132,7 @@ extern "C" ABFT_API abft_status abft_tune(const abft_grid* grids, int32_t n_grid
   double best_us = -1.0;
   abft_options win = *base;
   abft_status st = ABFT_OK;
-  for (const Cand& c : candidates(grids, n_grids)) {
+  for (const Cand& c : candidates(grids, n_grids, mode)) {
     const abft_options o = with(*base, c);
     const size_t need = abft_workspace_bytes(grids, n_grids, &o);
     if (need == 0 || need > workspace_bytes) continue;

@@ -1,0 +1,80 @@
+"""Temporal blocking: depth-k passes (k = 2, 3, 4) advance k unprotected sweeps at once
+on shared-memory levels with recomputed halos.  Every level uses the single sweep's
+point update and applies the flips of its own sweep to every point it computes, so
+the grids must equal depth-1 runs bit for bit, also across tile edges, ragged tails,
+flips in the halo, offline windows (the window's last sweep stays a protected single
+sweep) and rollbacks; and the oracle's values."""
+import numpy as np
+import pytest
+
+from paper_1909_00709_gb300 import inputs
+from _util import gpu_context, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+NONE, ONLINE, OFFLINE = 0, 1, 2
+SHAPES = [(200, 37, 5), (129, 17, 3), (300, 130, 40), (64, 64, 8), (1, 7, 1), (33, 1, 4), (257, 64, 9)]
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_00709_gb300 import abi, build
+    build.build()
+    abi.lib()
+    return abi
+
+
+def _flips(shape, steps, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(0, steps, 3):
+        # points on tile edges (x = 127/128, y = 7/8) and random ones, all bit positions
+        for x, y in ((min(127, nx - 1), min(7, ny - 1)), (min(128, nx - 1), min(8, ny - 1)),
+                     (int(rng.integers(nx)), int(rng.integers(ny)))):
+            out.append((t, 0, int(rng.integers(nz)), y, x, int(rng.integers(32))))
+    return inputs.flip_list(out)
+
+
+def _run(abi, shape, plan, flips, **opt):
+    with gpu_context(abi, [shape], [21], persistent=0, **opt) as ctx:
+        ctx.inject_list(flips)
+        for n, mode in plan:
+            ctx.step(n, mode)
+        ev = sorted(map(tuple, ctx.events()[["step", "z", "y", "x", "kind"]].tolist()))
+        return ctx.read(0), ev, ctx.counters()["rollbacks"]
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_unprotected_depth_k_equals_single_sweeps(abi, shape, depth):
+    steps = 13  # not a multiple of k: the remainder runs as single sweeps
+    fl = _flips(shape, steps, 4)
+    ref, _, _ = _run(abi, shape, [(steps, NONE)], fl, depth=1)
+    got, _, _ = _run(abi, shape, [(steps, NONE)], fl, depth=depth)
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+@pytest.mark.parametrize("shape", [(200, 37, 5), (300, 130, 40), (257, 64, 9)])
+def test_offline_windows_with_depth_equal_single_sweeps(abi, shape, depth):
+    plan = [(37, OFFLINE), (5, NONE), (16, OFFLINE), (3, ONLINE)]
+    fl = _flips(shape, 61, 8)
+    ref = _run(abi, shape, plan, fl, depth=1)
+    got = _run(abi, shape, plan, fl, depth=depth)
+    np.testing.assert_array_equal(got[0].view(np.uint32), ref[0].view(np.uint32))
+    assert got[1] == ref[1] and got[2] == ref[2]
+    assert ref[2] > 0  # some windows were rolled back
+
+
+@pytest.mark.parametrize("depth", [2, 4])
+def test_depth_k_matches_oracle(abi, orc, depth):
+    shape, steps = (200, 37, 5), 24
+    with gpu_context(abi, [shape], [3], persistent=0, depth=depth) as ctx:
+        ctx.step(steps, NONE)
+        got = ctx.read(0)
+    ref = oracle_run(orc, shape, 3, steps, orc.MODE_NONE)["u"]
+    assert rel_err(got, ref) < 1e-5 * max(1.0, steps / 100)
