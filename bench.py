@@ -387,7 +387,42 @@ def side_runs(dev, stream, flush):
                             "launches_per_sweep": (c.counters()["kernel_launches"] - l0) / sweeps}
             res["overhead_pct"] = (res["online"]["ms_per_sweep"] / res["unprotected"]["ms_per_sweep"] - 1) * 100
             batch[name] = res
-    return {"batch": batch,
+    # the paper's per-bit campaign (Sec. 5.3, Fig. 7): 64x64x8, eps 1e-5, 1000 flips per
+    # bit position, one per sweep at a random point; share located and corrected at the
+    # true point
+    camp = {}
+    cs = (64, 64, 8)
+    ct, cp = inputs.grid_inputs(*cs, seed=0)
+    for bit in range(32):
+        rng = np.random.default_rng(1000 + bit)
+        fl = [(t, 0, int(rng.integers(cs[2])), int(rng.integers(cs[1])), int(rng.integers(cs[0])), bit)
+              for t in range(1, 1001)]
+        with abi.Context([cs], [ct], [cp], [inputs.hotspot_coeffs(*cs)], device=dev, stream=stream) as c:
+            c.inject_list(inputs.flip_list(fl))
+            c.step(1001, abi.MODE_ONLINE)
+            ev = c.events()
+        got = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"])): int(e["kind"]) for e in ev}
+        camp[bit] = sum(1 for (t, _, z, y, x, _) in fl if got.get((t, z, y, x)) == 1) / 1000.0
+    campaign = {"shape": list(cs), "flips_per_bit": 1000, "eps": 1e-5, "corrected_share_by_bit": camp,
+                "lowest_always_corrected_bit": min(b for b in range(32) if all(camp[k] == 1.0 for k in range(b, 32)))}
+    # offline detection period (Sec. 5.4, Fig. 8): the benchmark grid, 1024 sweeps with
+    # seeded flips at 1e-3 per sweep, for periods 1..128
+    tt, tp = inputs.grid_inputs(*SHAPE, seed=1)
+    dsweep = {}
+    for delta in (1, 2, 4, 8, 16, 32, 64, 128):
+        with abi.Context([SHAPE], [tt], [tp], [inputs.hotspot_coeffs(*SHAPE)], device=dev, stream=stream,
+                         delta=delta) as c:
+            c.inject(1, RATE, 0xFFFFFFFF)
+            c.step(delta, abi.MODE_OFFLINE)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(1024, abi.MODE_OFFLINE)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            dsweep[delta] = {"glups": math.prod(SHAPE) * 1024 / (ms / 1e3) / 1e9, "rollbacks": c.counters()["rollbacks"]}
+    return {"batch": batch, "bit_campaign": campaign, "offline_period_sweep": dsweep,
             "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
                           "variants": prec},
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,

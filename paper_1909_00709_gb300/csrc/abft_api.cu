@@ -37,6 +37,15 @@ struct GridPlan {
   size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx;
 };
 
+// per-launch control words of a grid: fails[3], redo, bar, bars[3] (zeroed before every
+// persistent launch)
+constexpr size_t kLaunchCtrlBytes = offsetof(DevGridCtrl, verdict) - offsetof(DevGridCtrl, fails);
+static_assert(offsetof(DevGridCtrl, redo) == offsetof(DevGridCtrl, fails) + 3 * sizeof(unsigned) &&
+                  offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, redo) + sizeof(unsigned) &&
+                  offsetof(DevGridCtrl, bars) == offsetof(DevGridCtrl, bar) + sizeof(unsigned long long) &&
+                  offsetof(DevGridCtrl, verdict) == offsetof(DevGridCtrl, bars) + 3 * sizeof(unsigned long long),
+              "per-launch control words must be contiguous");
+
 struct Plan {
   std::vector<GridPlan> g;
   size_t ctrl, gctrl, events, flips, off, total;
@@ -479,11 +488,8 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
       p = other_than(c, ctx->ref[gi]);
       q = c;
     }
-    // zero the per-sweep fail counters and the barrier arrival count (contiguous)
-    static_assert(offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, fails) + 4 * sizeof(unsigned),
-                  "fails[] and bar must be contiguous");
-    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned) + sizeof(unsigned long long),
-                       ctx->stream));
+    // zero the per-sweep fail counters, redo flag and barrier counters (contiguous)
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, kLaunchCtrlBytes, ctx->stream));
     int blocks = 0;
     CK(run(ctx, prot ? kKPersistProt : kKPersistPlain, [&] {
       return launch_persistent(L, g, &ctx->tm_u[3 * gi], ctx->tm_c[gi], &ctx->tm_p[4 * gi], ctx->step, (int)n, c, p, q,
@@ -510,8 +516,7 @@ abft_status persistent_offline_all(abft_ctx* ctx, int64_t n) {
     abft_status s = ensure_checksums(ctx, gi);
     if (s) return s;
     const GridDev& g = ctx->g[gi];
-    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, 4 * sizeof(unsigned) + sizeof(unsigned long long),
-                       ctx->stream));
+    CK(cudaMemsetAsync(&ctx->gctrl[gi].fails[0], 0, kLaunchCtrlBytes, ctx->stream));
     int blocks = 0;
     const int ck = ctx->cur[gi];
     CK(run(ctx, kKPersistProt, [&] {

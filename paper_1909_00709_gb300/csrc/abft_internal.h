@@ -59,6 +59,7 @@ struct DevGridCtrl {
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
   unsigned int redo;         // persistent online kernel: 1 = every CTA recomputes the speculative sweep
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
+  unsigned long long bars[3];  // payload barrier (online kernel): per instance mod 3, arrivals | payload << 32
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
   unsigned long long max_resid;   // bits of the largest |a'-a|/|a| of a passing entry (when tracked)

@@ -183,6 +183,55 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, DevCtrl*
   return s_ok != 0;
 }
 
+// Grid barrier whose arrivals carry a payload (the online kernel's count of failing
+// entries, a shared-memory word that thread 0 takes and clears after the block has
+// synchronised), so that leaving the barrier also tells every CTA the total without a
+// second round trip.  Instance k (counted identically by every CTA) uses
+// counters[k % 3]: each arrival adds 1 + (payload << 32), and a CTA leaves when the
+// low half reaches the grid size; the high half is then the total.  Block 0, on leaving
+// instance k, clears the counter of instance k + 2 (last used by instance k - 1, which
+// every CTA has left, and not used again before block 0 arrives at instance k + 1).
+// Time-bounded like grid_barrier; returns false on timeout.
+static __device__ __forceinline__ bool grid_barrier_sum(unsigned long long* counters, unsigned k, unsigned* payload,
+                                                     DevCtrl* ctrl, unsigned* total) {
+  __shared__ int s_ok;
+  __shared__ unsigned s_tot;
+  __syncthreads();  // every thread's contribution to *payload is in
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned tot = 0;
+    const unsigned n = gridDim.x * gridDim.y * gridDim.z;
+    unsigned long long* c = counters + (k % 3u);
+    const unsigned long long add = 1ull | ((unsigned long long)(payload ? *payload : 0u) << 32);
+    if (payload) *payload = 0u;  // taken; cleared before the block moves on
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(c), "l"(add) : "memory");
+    unsigned long long seen;
+    unsigned long long t0 = 0;
+    for (unsigned spins = 0;; ++spins) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(c) : "memory");
+      if ((unsigned)(seen & 0xffffffffull) >= n) {
+        tot = (unsigned)(seen >> 32);
+        break;
+      }
+      if ((spins & 1023u) == 1023u) {
+        const unsigned long long t = globaltimer_ns();
+        if (t0 == 0) t0 = t;
+        if (t - t0 > kBarrierTimeoutNs || (ld_acquire_u32(&ctrl->status) & kStTimeout)) {
+          set_status(ctrl, kStTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (ok && blockIdx.x == 0) counters[(k + 2u) % 3u] = 0ull;
+    s_ok = ok;
+    s_tot = tot;
+  }
+  __syncthreads();
+  *total = s_tot;
+  return s_ok != 0;
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");

@@ -187,7 +187,10 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
     prefetch_tensormap(&a.tm_c);
   }
   __syncthreads();
-  unsigned long long* bar = &g.gc->bar;
+  unsigned long long* bars = g.gc->bars;
+  unsigned nbar = 0;  // barrier instances passed (identical in every CTA)
+  __shared__ unsigned s_fails, s_redo;
+  if (threadIdx.x == 0) s_fails = s_redo = 0;
   const int ntiles = g.ntx * g.nty;
   const bool resident_c = (int)gridDim.x >= ntiles;
   const bool sweeper = threadIdx.x < kSweepThreads;
@@ -212,8 +215,6 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
     const int cur = (a.first_in + k) % 3, nxt = (a.first_in + k + 1) % 3, prv = (a.first_in + k + 2) % 3;
     const int pb_cur = (int)(s & 1), pb_nxt = (int)((s + 1) & 1);
     const bool sweep = k < a.n_steps, check = k > 0;
-    unsigned* any = &g.gc->fails[s % 3];
-    if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[(s + 1) % 3] = 0;  // last read two sweeps ago
     if (sweeper) {
       // sweep warps: u^s -> u^{s+1}, partials into the other partial buffer
       if (sweep)
@@ -223,12 +224,15 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         }
     } else if (check) {
       // check warp, concurrently: u^s against the interpolation from a^{s-1}, b^{s-1}
-      for (int r = r0; r < r1; ++r) check_box_round<ACC>(g, a.tm_p, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, any);
+      for (int r = r0; r < r1; ++r)
+        check_box_round<ACC>(g, a.tm_p, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, &s_fails);
     }
-    ok = grid_barrier(bar, ctrl);
+    // the barrier carries this CTA's failing-entry count and returns the total
+    unsigned total = 0;
+    ok = grid_barrier_sum(bars, nbar++, &s_fails, ctrl, &total);
     if (!ok || !check) continue;
     // rare: locate, correct, repair the speculative sweep
-    if (ld_acquire_u32(any) != 0) {
+    if (total != 0) {
       if (blockIdx.x == 0) {
         // u^s is the output of sweep s - 1; u^{s+1} that of sweep s
         resolve_planes_into(rs, g, g.u[prv], g.u[cur], g.A[cur], g.B[cur], g.AP[0], g.BP[0], s - 1, ctrl, ev,
@@ -240,18 +244,20 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         if (sweep && !redo)
           repair_next<Tiles, TY, ACC>(g, g.u[cur], g.u[nxt], pb_nxt ? g.PA2 : g.PA, pb_nxt ? g.PB2 : g.PB, rs, s,
                                       ctrl, sched);
-        if (threadIdx.x == 0) g.gc->redo = redo ? 1u : 0u;
+        if (threadIdx.x == 0) s_redo = redo ? 1u : 0u;
         fence_proxy_async_global();
       }
-      ok = grid_barrier(bar, ctrl);
-      if (ok && sweep && ld_acquire_u32(&g.gc->redo) != 0) {
+      unsigned redo_all = 0;  // block 0's decision, carried by the barrier
+      ok = grid_barrier_sum(bars, nbar++, blockIdx.x == 0 ? &s_redo : nullptr, ctrl, &redo_all);
+      if (ok && sweep && redo_all != 0) {
         if (sweeper)
           for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, !resident_c);
             tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[nxt], tile % g.ntx, tile / g.ntx, ctrl,
                                           pb_nxt);
           }
-        ok = grid_barrier(bar, ctrl);
+        unsigned none = 0;
+        ok = grid_barrier_sum(bars, nbar++, nullptr, ctrl, &none);
       }
     }
   }
@@ -460,8 +466,10 @@ static cudaError_t launch_persist_ty(const Launch& L, const PersistArgs& a, bool
   }
 }
 
-// Whether the persistent kernel for this grid would give every CTA a single tile
-// (the case it is built for; larger grids keep one launch per sweep).
+// Whether the persistent kernel suits this grid: every CTA owns a single tile (the
+// case it is built for), or, for unprotected sweeps, at least two CTAs fit on an SM and
+// each CTA streams several tiles per sweep (measured faster than one launch per sweep
+// at 1024x1024x256; the online kernel with several tiles per CTA was slower).
 template <class Tiles, int TY>
 static bool fits_t(const GridDev& g, bool prot) {
   if (prot && (g.nty > 256 || g.ntx > 256)) return false;  // one TMA box per check round
@@ -474,7 +482,7 @@ static bool fits_t(const GridDev& g, bool prot) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, prot ? kOnlineThreads : 256, smem) != cudaSuccess)
     return false;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-  return (long long)g.ntx * g.nty <= (long long)per_sm * sms;
+  return (long long)g.ntx * g.nty <= (long long)per_sm * sms || (!prot && per_sm >= 2);
 }
 
 bool persistent_fits(const GridDev& g, bool prot) {
