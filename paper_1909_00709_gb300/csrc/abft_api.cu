@@ -324,6 +324,8 @@ struct abft_ctx {
   cudaEvent_t roles_ev = nullptr;
   bool roles_pending = false;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // concurrent tile classes (and their captured branch)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [unprotected, online]: graph_steps sweeps each
   // counters
   int64_t launches = 0, rollbacks = 0, flips_scheduled = 0;
@@ -666,10 +668,30 @@ int batch_kernels_per_sweep(const abft_ctx* ctx, bool prot) {
 // launches through run() (counting and timing), otherwise they are being captured
 cudaError_t batch_sweep(abft_ctx* ctx, const Launch& L, bool prot, bool counted) {
   const int acc = ctx->opt.acc;
-  for (const auto& b : ctx->bcls) {
+  // tile classes after the first run on a side stream, concurrently (their grids are
+  // disjoint); the check waits for all of them.  Sequential while kernels are timed.
+  const bool fork = ctx->bcls.size() > 1 && !ctx->timing;
+  if (fork) {
+    cudaError_t e = cudaSuccess;
+    if (!ctx->side_stream) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->fork_ev) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->join_ev) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_ev, L.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side_stream, ctx->fork_ev, 0);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t c = 0; c < ctx->bcls.size(); ++c) {
+    const auto& b = ctx->bcls[c];
     const BatchArgs a = batch_args(ctx, b);
-    auto f = [&] { return launch_sweep_batch(L, a, b.blocks, b.smem, b.shallow, b.ty, prot, acc); };
+    Launch Lc = L;
+    if (fork && c > 0) Lc.s = ctx->side_stream;
+    auto f = [&] { return launch_sweep_batch(Lc, a, b.blocks, b.smem, b.shallow, b.ty, prot, acc); };
     const cudaError_t e = counted ? run(ctx, prot ? kKSweepProt : kKSweepPlain, f) : f();
+    if (e != cudaSuccess) return e;
+  }
+  if (fork) {
+    cudaError_t e = cudaEventRecord(ctx->join_ev, ctx->side_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.s, ctx->join_ev, 0);
     if (e != cudaSuccess) return e;
   }
   if (!prot) return cudaSuccess;
@@ -997,6 +1019,9 @@ void abft_destroy(abft_ctx* ctx) {
   for (cudaGraphExec_t& x : ctx->graph)
     if (x) cudaGraphExecDestroy(x);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->roles_ev) cudaEventDestroy(ctx->roles_ev);
   if (ctx->h_roles) cudaFreeHost(ctx->h_roles);
   if (ctx->h_flips) cudaFreeHost(ctx->h_flips);
