@@ -361,14 +361,22 @@ def side_runs(dev, stream, flush):
                              ("offline_flips", abi.MODE_OFFLINE, lam)):
         large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511)
     # many uneven grids: batched launches (one sweep launch per tile class, one check
-    # launch per sweep, graphs of 50 sweeps) against the same grids advanced one by one
+    # launch per sweep, graphs of 50 sweeps, tiles autotuned; the unprotected run uses the
+    # same options) against the same grids advanced one by one
     shapes = inputs.batch_shapes(BATCH_GRIDS, seed=3)
-    bt, bp = zip(*[inputs.grid_inputs(*sh, seed=1000 + i) for i, sh in enumerate(shapes)])
+    bt, bp = [], []
+    for i, sh in enumerate(shapes):  # uploaded once, reused by the tuner and every context
+        t_, p_ = inputs.grid_inputs(*sh, seed=1000 + i)
+        bt.append(torch.from_numpy(t_).to(dev))
+        bp.append(torch.from_numpy(p_).to(dev))
     bc = [inputs.hotspot_coeffs(*sh) for sh in shapes]
     npts = sum(math.prod(sh) for sh in shapes)
-    batch = {"grids": BATCH_GRIDS, "points": npts, "flip_rate_per_sweep_and_grid": BATCH_RATE}
-    for name, opts, sweeps in (("batched", {"batch": 1}, 200), ("grid_by_grid", {"batch": 0}, 40)):
-        with abi.Context(list(shapes), list(bt), list(bp), bc, device=dev, stream=stream, **opts) as c:
+    t0 = time.perf_counter()
+    tuned, _ = abi.autotune(shapes, bt, bp, bc, abi.MODE_ONLINE, sweeps=10, device=dev, stream=stream)
+    batch = {"grids": BATCH_GRIDS, "points": npts, "flip_rate_per_sweep_and_grid": BATCH_RATE,
+             "tuned_options": tuned, "tuning_s": time.perf_counter() - t0}
+    for name, opts, sweeps in (("batched", dict(tuned, batch=1), 200), ("grid_by_grid", {"batch": 0}, 40)):
+        with abi.Context(list(shapes), bt, bp, bc, device=dev, stream=stream, **opts) as c:
             res = {}
             for mode, key in ((abi.MODE_NONE, "unprotected"), (abi.MODE_ONLINE, "online")):
                 if mode == abi.MODE_ONLINE:
@@ -406,13 +414,14 @@ def side_runs(dev, stream, flush):
     campaign = {"shape": list(cs), "flips_per_bit": 1000, "eps": 1e-5, "corrected_share_by_bit": camp,
                 "lowest_always_corrected_bit": min(b for b in range(32) if all(camp[k] == 1.0 for k in range(b, 32)))}
     # offline detection period (Sec. 5.4, Fig. 8): the benchmark grid, 1024 sweeps with
-    # seeded flips at 1e-3 per sweep, for periods 1..128
+    # seeded flips at 4e-3 per sweep (a few per run, so long windows pay for rollbacks),
+    # for periods 1..128
     tt, tp = inputs.grid_inputs(*SHAPE, seed=1)
     dsweep = {}
     for delta in (1, 2, 4, 8, 16, 32, 64, 128):
         with abi.Context([SHAPE], [tt], [tp], [inputs.hotspot_coeffs(*SHAPE)], device=dev, stream=stream,
                          delta=delta) as c:
-            c.inject(1, RATE, 0xFFFFFFFF)
+            c.inject(1, 4e-3, 0xFFFFFFFF)
             c.step(delta, abi.MODE_OFFLINE)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)

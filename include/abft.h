@@ -101,6 +101,9 @@ typedef struct {
   int32_t depth;            /* temporal blocking: unprotected sweeps (mode NONE, and the sweeps of
                                an offline window before its last) advance `depth` (1..4) sweeps per
                                pass over the grid where a grid is swept launch by launch; 1 = off */
+  int32_t overlap;          /* 1: a single grid checked online launch by launch (too large for the
+                               persistent kernel) runs each sweep's check beside the next sweep and
+                               recomputes that sweep only when the check corrected something */
   int32_t batch;            /* 1: a context with several grids advances them all with one sweep
                                launch per tile class and one check launch per sweep (CUDA graphs
                                of graph_steps sweeps); 0: grid by grid. Offline steps always go

@@ -42,7 +42,8 @@ class abft_options(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("acc", ct.c_int32),
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
-                ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("batch", ct.c_int32),
+                ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("overlap", ct.c_int32),
+                ("batch", ct.c_int32),
                 ("stream", ct.c_void_p)]
 
 
@@ -205,9 +206,16 @@ def autotune(shapes, temps, powers, coeffs, mode: int, sweeps: int = 20, *, devi
     if nbytes == 0:
         raise AbftError(1, "invalid grid shapes or options")
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    keep = [np.ascontiguousarray(a, dtype=np.float32) for a in list(temps) + list(powers)]
-    tp = (ct.c_void_p * n)(*[keep[i].ctypes.data for i in range(n)])
-    pp = (ct.c_void_p * n)(*[keep[n + i].ctypes.data for i in range(n)])
+
+    def ptr(a):  # device tensors are used in place, anything else through host memory
+        if isinstance(a, torch.Tensor):
+            assert a.dtype == torch.float32 and a.is_contiguous()
+            return a, a.data_ptr()
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        return a, a.ctypes.data
+    keep = [ptr(a) for a in list(temps) + list(powers)]
+    tp = (ct.c_void_p * n)(*[keep[i][1] for i in range(n)])
+    pp = (ct.c_void_p * n)(*[keep[n + i][1] for i in range(n)])
     cos = (abft_coeffs * n)(*[_coeffs(c) for c in coeffs])
     best = abft_options()
     us = ct.c_double()

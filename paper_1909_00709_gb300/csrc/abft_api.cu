@@ -74,7 +74,7 @@ bool valid_options(const abft_options& o) {
          o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
          (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1) &&
-         o.depth >= 1 && o.depth <= 4;
+         o.depth >= 1 && o.depth <= 4 && (o.overlap == 0 || o.overlap == 1);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -551,7 +551,7 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
       CK(run(ctx, kKSweepProt, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
       const PartialMaps* pm = reinterpret_cast<const PartialMaps*>(&ctx->tm_p[4 * gi]);
       CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(L, g, *pm, in, out); }));
-      CK(run(ctx, kKOther, [&] { return launch_resolve(L, g, in, out); }));
+      CK(run(ctx, kKOther, [&] { return launch_resolve(L, g, in, out, ctx->step); }));
       ctx->cur[gi] = out;
       ctx->ref[gi] = out;
       ctx->ref_step[gi] = ctx->step + 1;
@@ -564,6 +564,59 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
     }
   }
   ++ctx->step;
+  return ABFT_OK;
+}
+
+// `n` online sweeps of a single grid with the check of each sweep overlapping the next
+// sweep.  Sweep s+1 starts as soon as sweep s is done; the check and location of sweep
+// s run beside it on a side stream (one-warp box-check blocks fit next to the sweep's
+// CTAs) and write their fixes into u^{s+1} directly; a conditional recomputation of
+// sweep s+1 then runs only if a fix was made (its CTAs leave at once otherwise).
+// Partial checksums alternate between two buffers by sweep parity, so the sweep never
+// overwrites the partials its predecessor's check is reading.  Results equal the
+// sequential order bit for bit.
+abft_status online_overlap(abft_ctx* ctx, int64_t n) {
+  const int gi = 0;
+  const GridDev& g = ctx->g[gi];
+  Launch A = launcher(ctx);
+  cudaError_t e = cudaSuccess;
+  if (!ctx->side_stream) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->fork_ev) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->join_ev) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return fail(ctx, ABFT_E_CUDA, "overlap set-up: %s", cudaGetErrorString(e));
+  Launch B = A;
+  B.s = ctx->side_stream;
+  CK(cudaMemsetAsync(&ctx->gctrl[gi].redo, 0, sizeof(unsigned), A.s));
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t s = ctx->step;
+    const int in = ctx->cur[gi], out = (in + 1) % 3;
+    // this sweep's partial buffers (parity of s)
+    GridDev gs = g;
+    PartialMaps pm = *reinterpret_cast<const PartialMaps*>(&ctx->tm_p[4 * gi]);
+    if (s & 1) {
+      gs.PA = g.PA2;
+      gs.PB = g.PB2;
+      std::swap(pm.m[0], pm.m[1]);
+      std::swap(pm.m[2], pm.m[3]);
+    }
+    CK(run(ctx, kKSweepProt, [&] { return launch_sweep(A, gs, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
+    if (k > 0) {  // the previous sweep's check may have fixed u^s: recompute this sweep if so
+      CK(cudaStreamWaitEvent(A.s, ctx->join_ev, 0));
+      CK(run(ctx, kKOther,
+             [&] { return launch_sweep(A, gs, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true, 1); }));
+    }
+    CK(cudaEventRecord(ctx->fork_ev, A.s));
+    CK(cudaStreamWaitEvent(B.s, ctx->fork_ev, 0));
+    CK(run(ctx, kKCheckOnline, [&] { return launch_check_online(B, gs, pm, in, out, 1); }));
+    CK(run(ctx, kKOther, [&] { return launch_resolve(B, gs, in, out, s); }));
+    CK(cudaEventRecord(ctx->join_ev, B.s));
+    ctx->cur[gi] = out;
+    ctx->ref[gi] = out;
+    ctx->ref_step[gi] = s + 1;
+    ctx->ck_valid[gi] = 1;
+    ++ctx->step;
+  }
+  CK(cudaStreamWaitEvent(A.s, ctx->join_ev, 0));  // the last check and its fixes
   return ABFT_OK;
 }
 
@@ -963,6 +1016,7 @@ void abft_default_options(abft_options* o) {
   o->graph_steps = 50;
   o->batch = 1;
   o->depth = 1;
+  o->overlap = 1;
   o->tile_y = 0;
   o->max_flips_per_step = 64;
   o->persistent = 1;
@@ -1260,6 +1314,11 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
           s = ensure_checksums(ctx, gi);
           if (s) return s;
         }
+      if (mode == ABFT_MODE_ONLINE && ctx->n == 1 && ctx->opt.overlap && !ctx->timing) {
+        s = online_overlap(ctx, covered - k);
+        if (s) return s;
+        break;
+      }
       s = sweep_all(ctx, mode);
       if (s) return s;
     }

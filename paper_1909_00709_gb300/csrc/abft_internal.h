@@ -57,7 +57,7 @@ struct DevGridCtrl {
   unsigned int done_aux;
   unsigned int rollbacks;   // offline windows the persistent kernel recomputed
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
-  unsigned int redo;         // persistent online kernel: 1 = every CTA recomputes the speculative sweep
+  unsigned int redo;         // 1: a correction was made after the next sweep had started (per-launch overlap)
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
   unsigned long long bars[3];  // payload barrier (online kernel): per instance mod 3, arrivals | payload << 32
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
@@ -122,21 +122,27 @@ cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUte
 cudaError_t make_partial_maps(const GridDev& g, CUtensorMap tm[4], char* err, size_t errlen);
 constexpr int kCheckBox = 32;  // entries per check-warp round
 int sweep_smem_bytes(int ty, bool prot);
+// redo != 0: recompute the sweep just committed only if the location step flagged a
+// correction (the flag in the grid's counters), see k_sweep
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
-                         const CUtensorMap& tm_c, int in, int out, bool prot);
+                         const CUtensorMap& tm_c, int in, int out, bool prot, int redo = 0);
 cudaError_t launch_source_term(const Launch& L, const GridDev& g, const abft_coeffs& co);
 cudaError_t launch_checksums(const Launch& L, const GridDev& g, const float* u, double* A, double* B);
 // the tensor maps of a grid's partial buffers PA, PA2, PB, PB2 (make_partial_maps)
 struct PartialMaps {
   CUtensorMap m[4];
 };
-cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out);
+// max_warps caps the box check's warps per block (1 lets it run beside a sweep's CTAs)
+cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out,
+                                int max_warps = 8);
 // the box check needs at most 256 tiles along x and along y
 bool check_box_usable(const GridDev& g);
 int check_box_bytes_host(int nty, int ntx, int acc);
 int check_box_warps(int box_bytes);
 // location and correction after launch_check_online, one block per plane
-cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out);
+// `step`: the sweep whose output is checked (event stamps); a resolved plane sets the
+// grid's redo flag
+cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out, long long step);
 cudaError_t launch_reduce_partials(const Launch& L, const GridDev& g, int out);
 cudaError_t launch_chain(const Launch& L, const GridDev& g, const double* a_in, const double* b_in,
                          double* a_out, double* b_out);

@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(256)
     }
     __syncwarp();
     unsigned phase = 0;
+    const InterpW iw(g.k);
     const int rounds = check_rounds_of(g);
     for (int r = lb * nw + warp; r < rounds; r += nb * nw)
-      check_box_round<ACC>(g, tm_p, 0, 1, 0, r, buf, bar, phase, ctrl, nullptr);
+      check_box_round<ACC>(g, iw, tm_p, 0, 1, 0, r, buf, bar, phase, ctrl, nullptr);
   } else {
     check_warps<ACC>(g, 0, 1, lb * nw + warp, nb * nw, g.nz * (g.nx + g.ny));
   }

@@ -46,28 +46,30 @@ __global__ void __launch_bounds__(256)
   }
   __syncwarp();
   unsigned phase = 0;
+  const InterpW iw(g.k);
   const int rounds = check_rounds_of(g);
   for (int r = blockIdx.x * nw + warp; r < rounds; r += gridDim.x * nw)
-    check_box_round<ACC>(g, pm.m, in, out, 0, r, buf, bar, phase, ctrl, nullptr);
+    check_box_round<ACC>(g, iw, pm.m, in, out, 0, r, buf, bar, phase, ctrl, nullptr);
 }
 
 // Location and correction (Sec. 3.5) after the online check of the sweep just done,
 // one block per plane with failing entries (planes are independent): a single
 // intersection by Eq. (8), other patterns by recomputing lines from u[in].
 __global__ void __launch_bounds__(kCheckThreads)
-    k_resolve(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
+    k_resolve(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev, long long step) {
   __shared__ ResolveSmem sm;
   __shared__ int s_hit;
   if (threadIdx.x == 0) sm.nfix = 0;
-  const long long step = g.gc->step - 1;
   for (int z = blockIdx.x; z < g.nz; z += gridDim.x) {
     if (threadIdx.x == 0) s_hit = (__ldcg(&g.fcnt[2 * z]) | __ldcg(&g.fcnt[2 * z + 1])) != 0;
     __syncthreads();
     const bool hit = s_hit != 0;
     __syncthreads();  // every thread has read s_hit before thread 0 rewrites it
-    if (hit)
+    if (hit) {
       resolve_plane(sm, g, g.u[in], g.u[out], g.A[out], g.B[out], g.AP[0], g.BP[0], step, ctrl, ev,
                     &g.gc->unresolved, z);
+      if (threadIdx.x == 0) atomicExch(&g.gc->redo, 1u);  // u[out] changed: a started next sweep is stale
+    }
   }
 }
 
@@ -208,13 +210,14 @@ bool check_box_usable(const GridDev& g) { return g.nty <= 256 && g.ntx <= 256; }
 
 int check_box_bytes_host(int nty, int ntx, int acc) { return check_box_bytes(nty, ntx, acc); }
 
-cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out) {
+cudaError_t launch_check_online(const Launch& L, const GridDev& g, const PartialMaps& pm, int in, int out,
+                                int max_warps) {
   if (check_box_usable(g)) {
     const int box = (check_box_bytes(g.nty, g.ntx, g.acc) + 127) / 128 * 128;
-    const int nw = check_box_warps(box);
+    const int nw = std::min(check_box_warps(box), std::max(max_warps, 1));
     const int smem = 256 + nw * box;
     const long long rounds = (long long)g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
-    const int blocks = (int)std::min<long long>((rounds + nw - 1) / nw, 4LL * sm_count());
+    const int blocks = (int)std::min<long long>((rounds + nw - 1) / nw, (nw == 1 ? 8LL : 4LL) * sm_count());
     cudaError_t e = cudaSuccess;
     switch (g.acc) {
       case ABFT_ACC_TWOSUM:
@@ -244,8 +247,8 @@ cudaError_t launch_check_online(const Launch& L, const GridDev& g, const Partial
   return cudaGetLastError();
 }
 
-cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out) {
-  k_resolve<<<std::min(g.nz, 1024), kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events);
+cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out, long long step) {
+  k_resolve<<<std::min(g.nz, 1024), kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events, step);
   return cudaGetLastError();
 }
 

@@ -491,9 +491,9 @@ __device__ __forceinline__ int check_rounds_of(const GridDev& g) {
 }
 
 template <int ACC>
-__device__ __forceinline__ void check_box_round(const GridDev& g, const CUtensorMap* tm_p, int in, int out, int pbuf,
-                                                int round, unsigned char* buf, uint64_t* cbar, unsigned& phase,
-                                                DevCtrl* ctrl, unsigned* any) {
+__device__ __forceinline__ void check_box_round(const GridDev& g, const InterpW& w, const CUtensorMap* tm_p, int in,
+                                                int out, int pbuf, int round, unsigned char* buf, uint64_t* cbar,
+                                                unsigned& phase, DevCtrl* ctrl, unsigned* any) {
   using T = typename PartialType<ACC>::T;
   constexpr int per = ACC == ABFT_ACC_TWOSUM ? 2 : 1;
   const int lane = threadIdx.x & 31;
@@ -573,12 +573,12 @@ __device__ __forceinline__ void check_box_round(const GridDev& g, const CUtensor
   double p;
   if (is_a) {
     const double edge = asym ? edge_term(k.cn, k.cs, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cn, k.cs), k.cw, k.ce, k.cb, k.ct, edge);
+    p = interp(cc, v0, v1, v2, v3, v4, w.a0, w.cw, w.ce, w.cb, w.ct, edge);
     g.A[out][(size_t)z * len + idx] = s;
     g.AP[0][(size_t)z * len + idx] = p;
   } else {
     const double edge = asym ? edge_term(k.cw, k.ce, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, weight_sum3(k.cc, k.cw, k.ce), k.cn, k.cs, k.cb, k.ct, edge);
+    p = interp(cc, v0, v1, v2, v3, v4, w.b0, w.cn, w.cs, w.cb, w.ct, edge);
     g.B[out][(size_t)z * len + idx] = s;
     g.BP[0][(size_t)z * len + idx] = p;
   }

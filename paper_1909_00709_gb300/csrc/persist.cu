@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         }
     } else if (check) {
       // check warp, concurrently: u^s against the interpolation from a^{s-1}, b^{s-1}
+      const InterpW iw(g.k);
       for (int r = r0; r < r1; ++r)
-        check_box_round<ACC>(g, a.tm_p, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, &s_fails);
+        check_box_round<ACC>(g, iw, a.tm_p, prv, cur, pb_cur, r, cbuf, cbar, cphase, ctrl, &s_fails);
     }
     // the barrier carries this CTA's failing-entry count and returns the total
     unsigned total = 0;

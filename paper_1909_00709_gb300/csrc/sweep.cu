@@ -22,11 +22,16 @@ namespace abft {
 
 // One sweep of one grid: one CTA per tile.  The last CTA to finish commits the sweep
 // by advancing the grid's step counter (it drives injection and event stamps).
+// redo != 0: the conditional recomputation of the sweep just committed (used when the
+// next sweep was started before the previous check had finished): every CTA leaves at
+// once unless the location step flagged a correction, the sweep index is the committed
+// one, and the last CTA clears the flag instead of advancing the step.
 template <class Tiles, bool PROT, int ACC>
 __global__ void __launch_bounds__(256, 2)
     k_sweep(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c,
-            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
+            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched, int redo) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (redo && __ldcg(&g.gc->redo) == 0) return;  // uniform: the flag only changes after every CTA
   sched.load(ctrl);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
@@ -35,7 +40,7 @@ __global__ void __launch_bounds__(256, 2)
     prefetch_tensormap(&tm_c);
   }
   __syncthreads();
-  const long long step = g.gc->step;
+  const long long step = g.gc->step - (redo ? 1 : 0);
   const int txi = blockIdx.x % g.ntx, tyi = blockIdx.x / g.ntx;
   tiles.issue(&tm_u, &tm_c, g, txi, tyi, step, ctrl, sched, true);
   tiles.template run<PROT, ACC>(&tm_u, &tm_c, g, uout, txi, tyi, ctrl, 0);
@@ -44,7 +49,8 @@ __global__ void __launch_bounds__(256, 2)
     const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
     if (ticket == gridDim.x - 1) {
       g.gc->done_sweep = 0;
-      g.gc->step = step + 1;
+      if (redo) g.gc->redo = 0;
+      else g.gc->step = step + 1;
       __threadfence();
     }
   }
@@ -62,40 +68,40 @@ int sweep_smem_bytes(int ty, bool) {
 
 template <class Tiles, bool PROT, int ACC>
 static cudaError_t launch_t(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                            int out) {
+                            int out, int redo) {
   auto kern = k_sweep<Tiles, PROT, ACC>;
   const int smem = Tiles::smem_bytes(g.nz);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[out], L.ctrl, L.sched);
+  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[out], L.ctrl, L.sched, redo);
   return cudaGetLastError();
 }
 
 template <class Tiles>
 static cudaError_t launch_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                                int out, bool prot) {
-  if (!prot) return launch_t<Tiles, false, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out);
+                                int out, bool prot, int redo) {
+  if (!prot) return launch_t<Tiles, false, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out, redo);
   switch (g.acc) {
-    case ABFT_ACC_TWOSUM: return launch_t<Tiles, true, ABFT_ACC_TWOSUM>(L, g, tm_in, tm_c, out);
-    case ABFT_ACC_FP64: return launch_t<Tiles, true, ABFT_ACC_FP64>(L, g, tm_in, tm_c, out);
-    default: return launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out);
+    case ABFT_ACC_TWOSUM: return launch_t<Tiles, true, ABFT_ACC_TWOSUM>(L, g, tm_in, tm_c, out, redo);
+    case ABFT_ACC_FP64: return launch_t<Tiles, true, ABFT_ACC_FP64>(L, g, tm_in, tm_c, out, redo);
+    default: return launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out, redo);
   }
 }
 
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c, int in,
-                         int out, bool prot) {
+                         int out, bool prot, int redo) {
   (void)in;
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return launch_tiles<ShallowTiles<8>>(L, g, tm_in, tm_c, out, prot);
-      case 16: return launch_tiles<ShallowTiles<16>>(L, g, tm_in, tm_c, out, prot);
+      case 8: return launch_tiles<ShallowTiles<8>>(L, g, tm_in, tm_c, out, prot, redo);
+      case 16: return launch_tiles<ShallowTiles<16>>(L, g, tm_in, tm_c, out, prot, redo);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return launch_tiles<StreamTiles<8>>(L, g, tm_in, tm_c, out, prot);
-    case 16: return launch_tiles<StreamTiles<16>>(L, g, tm_in, tm_c, out, prot);
-    case 32: return launch_tiles<StreamTiles<32>>(L, g, tm_in, tm_c, out, prot);
+    case 8: return launch_tiles<StreamTiles<8>>(L, g, tm_in, tm_c, out, prot, redo);
+    case 16: return launch_tiles<StreamTiles<16>>(L, g, tm_in, tm_c, out, prot, redo);
+    case 32: return launch_tiles<StreamTiles<32>>(L, g, tm_in, tm_c, out, prot, redo);
     default: return cudaErrorInvalidValue;
   }
 }

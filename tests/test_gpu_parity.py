@@ -172,6 +172,26 @@ def test_persistent_heavy_flips_recompute_the_speculative_sweep(abi, orc, shape,
     assert rel_err(out[1][0], ref["u"]) < value_tol(steps)
 
 
+@pytest.mark.parametrize("rate", [0.0, 0.7, 40.0])
+@pytest.mark.parametrize("shape", [(300, 130, 40), (257, 64, 9)])
+def test_overlapped_check_matches_sequential(abi, shape, rate):
+    """Per-launch online sweeps with each check running beside the next sweep (and the
+    conditional recomputation when it corrected something) equal the sequential order
+    bit for bit, events included."""
+    out = []
+    for overlap in (0, 1):
+        with gpu_context(abi, [shape], [17], persistent=0, overlap=overlap, max_flips_per_step=64) as ctx:
+            if rate:
+                ctx.inject(5, rate, 0xFFFFFFFF)
+            ctx.step(9, ONLINE)
+            ctx.step(14, ONLINE)
+            out.append((ctx.read(0), sorted(map(tuple, ctx.events()[["step", "z", "y", "x", "kind"]].tolist()))))
+    np.testing.assert_array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    assert out[0][1] == out[1][1]
+    if rate:
+        assert len(out[0][1]) > 0
+
+
 FIXUP_CASES = {
     # flips in consecutive sweeps at neighbouring points: when sweep 5's flip is
     # corrected, the repaired output of sweep 6 must still carry sweep 6's flip
