@@ -93,7 +93,9 @@ typedef struct {
   int32_t tile_y;           /* rows per sweep tile (8, 16 or 32); 0 = library default */
   int32_t max_flips_per_step; /* schedule capacity per step and grid (<= 511) */
   int32_t persistent;       /* 1: run online/unprotected sweeps in one persistent cooperative
-                               launch per grid and schedule chunk; 0: one launch per kernel */
+                               launch per grid and schedule chunk where the grid's tiles fit one per
+                               CTA (unprotected: also several per CTA when two CTAs fit per SM);
+                               0: one launch per kernel */
   int32_t shallow;          /* 1: grids with nz <= 16 use whole-column tiles (all planes staged
                                at once); 0: always stream the planes */
   int32_t track_residual;   /* 1: keep the largest relative residual |a'-a|/|a| of the entries
@@ -134,7 +136,8 @@ typedef struct {
 
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
    sweeps, default tile, 64 flips per step, persistent launches, whole-column tiles for
-   shallow grids, NULL stream. */
+   shallow grids, no residual tracking, depth 1, overlapped checks, batched launches,
+   NULL stream. */
 ABFT_API void abft_default_options(abft_options* opt);
 
 /* Bytes of device workspace abft_init needs for these grids and options

@@ -427,9 +427,9 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       issue(z - 1 + S);
     }
     if (PROT && SMEM_EPI) {
-      // one warp per plane (rotating) reduces the plane's partials: four columns per
-      // lane over the eight warps in order, and row `lane` over its 32 lane partials
-      // by the butterfly's own pairing (the same sums as row_store, bit for bit)
+      // two warps per plane (rotating with z) reduce the plane's partials: one sums four
+      // columns per lane over the eight warps in order, the other row `lane` over its 32
+      // lane partials by the butterfly's own pairing (the same sums as row_store)
       if (warp == (z & (NW - 1))) {
         const float* r = reinterpret_cast<const float*>(red);
         float4 c = reinterpret_cast<const float4*>(r)[lane];
@@ -439,6 +439,8 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
           c.x += q.x; c.y += q.y; c.z += q.z; c.w += q.w;
         }
         *reinterpret_cast<float4*>(static_cast<float*>(PA) + ((size_t)tyi * nz + z) * g.pa_stride + x0 + 4 * lane) = c;
+      }
+      if (warp == ((z + NW / 2) & (NW - 1))) {
         if (lane < TY && y0 + lane < g.ny) {
           float t[32];
 #pragma unroll
