@@ -39,7 +39,7 @@ BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) of one 200-sweep launch of the dominant kernel, from one ncu
 # capture of this build (the working set stays in L2); None for kernels not captured
-TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 16993024 + 219904}
+TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 17055488 + 200704}
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
@@ -431,7 +431,28 @@ def side_runs(dev, stream, flush):
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1)
             dsweep[delta] = {"glups": math.prod(SHAPE) * 1024 / (ms / 1e3) / 1e9, "rollbacks": c.counters()["rollbacks"]}
-    return {"batch": batch, "bit_campaign": campaign, "offline_period_sweep": dsweep,
+    # the paper's accuracy experiment (Sec. 5.2, Eq. 9): 64x64x8, 128 sweeps, one flip at a
+    # random sweep, point and bit per run; l2 distance from the fault-free final grid
+    nx_, ny_, nz_ = cs
+    with abi.Context([cs], [ct], [cp], [inputs.hotspot_coeffs(*cs)], device=dev, stream=stream) as c:
+        c.step(128, abi.MODE_NONE)
+        uref = c.read(0).astype(np.float64)
+    rng = np.random.default_rng(77)
+    runs = [(int(rng.integers(128)), 0, int(rng.integers(nz_)), int(rng.integers(ny_)), int(rng.integers(nx_)),
+             int(rng.integers(32))) for _ in range(200)]
+    errcamp = {"shape": list(cs), "sweeps": 128, "runs": len(runs)}
+    for mode, name in ((abi.MODE_NONE, "unprotected"), (abi.MODE_ONLINE, "online"), (abi.MODE_OFFLINE, "offline")):
+        errs = []
+        for f in runs:
+            with abi.Context([cs], [ct], [cp], [inputs.hotspot_coeffs(*cs)], device=dev, stream=stream) as c:
+                c.inject_list(inputs.flip_list([f]))
+                c.step(128, mode)
+                d = c.read(0).astype(np.float64) - uref
+            errs.append(float(np.sqrt(np.sum(d * d))) if np.all(np.isfinite(d)) else float("inf"))
+        errs = np.array(errs)
+        errcamp[name] = {"median_l2": float(np.median(errs)), "mean_l2": float(np.mean(errs[np.isfinite(errs)])),
+                         "share_exact": float(np.mean(errs == 0.0))}
+    return {"batch": batch, "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
             "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
                           "variants": prec},
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,
