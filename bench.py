@@ -357,8 +357,8 @@ def side_runs(dev, stream, flush):
     large = {}
     lam = 1e-6 * math.prod(LARGE_SHAPE)  # flips per sweep
     for name, mode, rate in (("unprotected", abi.MODE_NONE, 0.0), ("online", abi.MODE_ONLINE, 0.0),
-                             ("offline", abi.MODE_OFFLINE, 0.0), ("online_flips", abi.MODE_ONLINE, lam),
-                             ("offline_flips", abi.MODE_OFFLINE, lam)):
+                             ("offline", abi.MODE_OFFLINE, 0.0), ("online_1_flip_per_sweep", abi.MODE_ONLINE, 1.0),
+                             ("online_flips", abi.MODE_ONLINE, lam), ("offline_flips", abi.MODE_OFFLINE, lam)):
         large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511)
     # many uneven grids: batched launches (one sweep launch per tile class, one check
     # launch per sweep, graphs of 50 sweeps, tiles autotuned; the unprotected run uses the
@@ -441,10 +441,12 @@ def side_runs(dev, stream, flush):
     runs = [(int(rng.integers(128)), 0, int(rng.integers(nz_)), int(rng.integers(ny_)), int(rng.integers(nx_)),
              int(rng.integers(32))) for _ in range(200)]
     errcamp = {"shape": list(cs), "sweeps": 128, "runs": len(runs)}
-    for mode, name in ((abi.MODE_NONE, "unprotected"), (abi.MODE_ONLINE, "online"), (abi.MODE_OFFLINE, "offline")):
+    for mode, name, acc in ((abi.MODE_NONE, "unprotected", 0), (abi.MODE_ONLINE, "online", 0),
+                            (abi.MODE_ONLINE, "online_twosum", 1), (abi.MODE_OFFLINE, "offline", 0)):
         errs = []
         for f in runs:
-            with abi.Context([cs], [ct], [cp], [inputs.hotspot_coeffs(*cs)], device=dev, stream=stream) as c:
+            with abi.Context([cs], [ct], [cp], [inputs.hotspot_coeffs(*cs)], device=dev, stream=stream,
+                             acc=acc) as c:
                 c.inject_list(inputs.flip_list([f]))
                 c.step(128, mode)
                 d = c.read(0).astype(np.float64) - uref

@@ -34,7 +34,7 @@ struct Bump {
 };
 
 struct GridPlan {
-  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx;
+  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx, tdirty;
 };
 
 // per-launch control words of a grid: fails[3], redo, bar, bars[3] (zeroed before every
@@ -102,6 +102,7 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     p.PB2 = b.take(ntx * G.nz * align_up(G.ny, 4) * partial_elem(o.acc));
     p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
+    p.tdirty = b.take(ntx * nty * sizeof(int));
   }
   P->ctrl = b.take(sizeof(DevCtrl));
   P->gctrl = b.take(sizeof(DevGridCtrl) * n);
@@ -1169,6 +1170,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.PB2 = ws + p.PB2;
     g.fcnt = (int*)(ws + p.fcnt);
     g.fidx = (int*)(ws + p.fidx);
+    g.tdirty = (int*)(ws + p.tdirty);
     g.gc = ctx->gctrl + i;
   }
   ctx->tm_u.resize(3 * n_grids);

@@ -86,6 +86,7 @@ struct GridDev {
   void* PA2; void* PB2;     // second set: the persistent kernel alternates by sweep parity
   int* fcnt;                // [nz][2] failing-entry counts (a, b)
   int* fidx;                // [nz][2][kFCap] failing indices
+  int* tdirty;              // [nty][ntx] tiles whose sweep must be redone after a late correction
   DevGridCtrl* gc;
 };
 

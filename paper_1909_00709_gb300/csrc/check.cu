@@ -68,7 +68,23 @@ __global__ void __launch_bounds__(kCheckThreads)
     if (hit) {
       resolve_plane(sm, g, g.u[in], g.u[out], g.A[out], g.B[out], g.AP[0], g.BP[0], step, ctrl, ev,
                     &g.gc->unresolved, z);
-      if (threadIdx.x == 0) atomicExch(&g.gc->redo, 1u);  // u[out] changed: a started next sweep is stale
+      // u[out] changed: a next sweep already started is stale in every tile whose
+      // stencil read a changed point (tiles span all planes, so only x and y matter)
+      if (threadIdx.x == 0) {
+        for (int k = 0; k < min(sm.nfix, kFixCap); ++k) {
+          const int4 f = sm.fix[k];  // (kind, z, y, x)
+          const bool all_y = f.x == kFixPlane || f.x == kFixCol, all_x = f.x == kFixPlane || f.x == kFixRow;
+          const int y0 = all_y ? 0 : max(f.z - 1, 0) / g.ty, y1 = all_y ? g.nty - 1 : min(f.z + 1, g.ny - 1) / g.ty;
+          const int x0 = all_x ? 0 : max(f.w - 1, 0) / kTX, x1 = all_x ? g.ntx - 1 : min(f.w + 1, g.nx - 1) / kTX;
+          for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) g.tdirty[ty * g.ntx + tx] = 1;
+        }
+        if (sm.nfix > kFixCap)  // the list overflowed: every tile
+          for (int t = 0; t < g.ntx * g.nty; ++t) g.tdirty[t] = 1;
+        sm.nfix = 0;
+        atomicExch(&g.gc->redo, 1u);
+      }
+      __syncthreads();
     }
   }
 }

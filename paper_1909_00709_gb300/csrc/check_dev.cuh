@@ -238,15 +238,34 @@ static __device__ void recompute_lines(const GridDev& g, int z, const float* uin
         u[pl + (size_t)y * g.px + sm.fa[k]] = point_update(g, uin, z, y, sm.fa[k]);
   }
   __syncthreads();
+  // the plane's checksums again in compensated FP32 (TwoSum pairs widened once, as the
+  // check sums its partials; GB300's FP64 rate would make a million FP64 additions per
+  // plane the slowest step) and a fixed order: a[x] by one thread per column with eight
+  // interleaved pairs (rows y = j mod 8, merged in order), b[y] by one warp per row
+  // (lane pairs over x = lane mod 32, merged by the butterfly)
   for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-    double s = 0.0;
-    for (int y = 0; y < g.ny; ++y) s += (double)__ldcg(u + pl + (size_t)y * g.px + x);
-    A[(size_t)z * g.nx + x] = s;
+    LaneSum L[8];
+    int y = 0;
+    for (; y + 8 <= g.ny; y += 8)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) L[j].add(__ldcg(u + pl + (size_t)(y + j) * g.px + x));
+    for (int j = 0; y + j < g.ny; ++j) L[j].add(__ldcg(u + pl + (size_t)(y + j) * g.px + x));
+#pragma unroll
+    for (int j = 1; j < 8; ++j) L[0].merge<ABFT_ACC_TWOSUM>(L[j]);
+    A[(size_t)z * g.nx + x] = L[0].total<ABFT_ACC_TWOSUM>();
   }
-  for (int y = threadIdx.x; y < g.ny; y += blockDim.x) {
-    double s = 0.0;
-    for (int x = 0; x < g.nx; ++x) s += (double)__ldcg(u + pl + (size_t)y * g.px + x);
-    B[(size_t)z * g.ny + y] = s;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int y = threadIdx.x >> 5; y < g.ny; y += nw) {
+    LaneSum t;
+    for (int x = lane; x < g.nx; x += 32) t.add(__ldcg(u + pl + (size_t)y * g.px + x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      LaneSum q;
+      q.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
+      q.lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
+      t.merge<ABFT_ACC_TWOSUM>(q);
+    }
+    if (lane == 0) B[(size_t)z * g.ny + y] = t.total<ABFT_ACC_TWOSUM>();
   }
   if (threadIdx.x == 0) {
     if (all) {

@@ -22,16 +22,29 @@ namespace abft {
 
 // One sweep of one grid: one CTA per tile.  The last CTA to finish commits the sweep
 // by advancing the grid's step counter (it drives injection and event stamps).
-// redo != 0: the conditional recomputation of the sweep just committed (used when the
+// REDO: the conditional recomputation of the sweep just committed (used when the
 // next sweep was started before the previous check had finished): every CTA leaves at
-// once unless the location step flagged a correction, the sweep index is the committed
-// one, and the last CTA clears the flag instead of advancing the step.
-template <class Tiles, bool PROT, int ACC>
+// once unless the location step flagged a correction; then only the tiles it marked
+// are recomputed (for the committed sweep index), and the last CTA clears the flag
+// instead of advancing the step.
+template <class Tiles, bool PROT, int ACC, bool REDO>
 __global__ void __launch_bounds__(256, 2)
     k_sweep(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c,
-            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched, int redo) {
+            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
+  constexpr bool redo = REDO;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (redo && __ldcg(&g.gc->redo) == 0) return;  // uniform: the flag only changes after every CTA
+  if (redo && __ldcg(&g.tdirty[blockIdx.x]) == 0) {  // this tile needs no recomputation
+    if (threadIdx.x == 0) {
+      const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
+      if (ticket == gridDim.x - 1) {
+        g.gc->done_sweep = 0;
+        g.gc->redo = 0;
+        __threadfence();
+      }
+    }
+    return;
+  }
   sched.load(ctrl);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
@@ -47,6 +60,7 @@ __global__ void __launch_bounds__(256, 2)
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
+    if (redo) g.tdirty[blockIdx.x] = 0;
     if (ticket == gridDim.x - 1) {
       g.gc->done_sweep = 0;
       if (redo) g.gc->redo = 0;
@@ -69,11 +83,11 @@ int sweep_smem_bytes(int ty, bool) {
 template <class Tiles, bool PROT, int ACC>
 static cudaError_t launch_t(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
                             int out, int redo) {
-  auto kern = k_sweep<Tiles, PROT, ACC>;
+  auto kern = redo ? k_sweep<Tiles, PROT, ACC, true> : k_sweep<Tiles, PROT, ACC, false>;
   const int smem = Tiles::smem_bytes(g.nz);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[out], L.ctrl, L.sched, redo);
+  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[out], L.ctrl, L.sched);
   return cudaGetLastError();
 }
 
