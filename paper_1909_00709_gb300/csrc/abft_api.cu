@@ -102,7 +102,7 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     p.PB2 = b.take(ntx * G.nz * align_up(G.ny, 4) * partial_elem(o.acc));
     p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
-    p.tdirty = b.take(ntx * nty * sizeof(int));
+    p.tdirty = b.take(2 * ntx * nty * sizeof(int));
   }
   P->ctrl = b.take(sizeof(DevCtrl));
   P->gctrl = b.take(sizeof(DevGridCtrl) * n);
@@ -604,7 +604,7 @@ abft_status online_overlap(abft_ctx* ctx, int64_t n) {
     if (k > 0) {  // the previous sweep's check may have fixed u^s: recompute this sweep if so
       CK(cudaStreamWaitEvent(A.s, ctx->join_ev, 0));
       CK(run(ctx, kKOther,
-             [&] { return launch_sweep(A, gs, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true, 1); }));
+             [&] { return launch_redo_tiles(A, gs, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out); }));
     }
     CK(cudaEventRecord(ctx->fork_ev, A.s));
     CK(cudaStreamWaitEvent(B.s, ctx->fork_ev, 0));

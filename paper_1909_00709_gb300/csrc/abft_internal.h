@@ -86,7 +86,8 @@ struct GridDev {
   void* PA2; void* PB2;     // second set: the persistent kernel alternates by sweep parity
   int* fcnt;                // [nz][2] failing-entry counts (a, b)
   int* fidx;                // [nz][2][kFCap] failing indices
-  int* tdirty;              // [nty][ntx] tiles whose sweep must be redone after a late correction
+  int* tdirty;              // [2][nty*ntx] per tile: highest marked plane + 1, nz - lowest marked plane
+                            // (0 = clean): planes whose sweep must be repaired after a late correction
   DevGridCtrl* gc;
 };
 
@@ -123,10 +124,12 @@ cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUte
 cudaError_t make_partial_maps(const GridDev& g, CUtensorMap tm[4], char* err, size_t errlen);
 constexpr int kCheckBox = 32;  // entries per check-warp round
 int sweep_smem_bytes(int ty, bool prot);
-// redo != 0: recompute the sweep just committed only if the location step flagged a
-// correction (the flag in the grid's counters), see k_sweep
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
-                         const CUtensorMap& tm_c, int in, int out, bool prot, int redo = 0);
+                         const CUtensorMap& tm_c, int in, int out, bool prot);
+// repair the sweep in -> out just committed where a late correction of u[in] reached
+// (tiles and planes marked by k_resolve; nothing unless the grid's redo flag is set)
+cudaError_t launch_redo_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
+                              int in, int out);
 cudaError_t launch_source_term(const Launch& L, const GridDev& g, const abft_coeffs& co);
 cudaError_t launch_checksums(const Launch& L, const GridDev& g, const float* u, double* A, double* B);
 // the tensor maps of a grid's partial buffers PA, PA2, PB, PB2 (make_partial_maps)

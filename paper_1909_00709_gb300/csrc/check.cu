@@ -71,16 +71,21 @@ __global__ void __launch_bounds__(kCheckThreads)
       // u[out] changed: a next sweep already started is stale in every tile whose
       // stencil read a changed point (tiles span all planes, so only x and y matter)
       if (threadIdx.x == 0) {
-        for (int k = 0; k < min(sm.nfix, kFixCap); ++k) {
-          const int4 f = sm.fix[k];  // (kind, z, y, x)
+        const int ntiles = g.ntx * g.nty;
+        int* hi1 = g.tdirty;            // highest marked plane + 1
+        int* lorev = g.tdirty + ntiles;  // nz - lowest marked plane
+        const bool every = sm.nfix > kFixCap;  // the list overflowed: the whole plane
+        for (int k = 0; k < (every ? 1 : sm.nfix); ++k) {
+          const int4 f = every ? make_int4(kFixPlane, z, -1, -1) : sm.fix[k];  // (kind, z, y, x)
           const bool all_y = f.x == kFixPlane || f.x == kFixCol, all_x = f.x == kFixPlane || f.x == kFixRow;
           const int y0 = all_y ? 0 : max(f.z - 1, 0) / g.ty, y1 = all_y ? g.nty - 1 : min(f.z + 1, g.ny - 1) / g.ty;
           const int x0 = all_x ? 0 : max(f.w - 1, 0) / kTX, x1 = all_x ? g.ntx - 1 : min(f.w + 1, g.nx - 1) / kTX;
           for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) g.tdirty[ty * g.ntx + tx] = 1;
+            for (int tx = x0; tx <= x1; ++tx) {
+              atomicMax(&hi1[ty * g.ntx + tx], f.y + 1);
+              atomicMax(&lorev[ty * g.ntx + tx], g.nz - f.y);
+            }
         }
-        if (sm.nfix > kFixCap)  // the list overflowed: every tile
-          for (int t = 0; t < g.ntx * g.nty; ++t) g.tdirty[t] = 1;
         sm.nfix = 0;
         atomicExch(&g.gc->redo, 1u);
       }

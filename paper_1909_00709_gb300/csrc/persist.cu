@@ -75,21 +75,6 @@ __global__ void __launch_bounds__(256, 2)
   if (ok && blockIdx.x == 0 && threadIdx.x == 0) g.gc->step = a.step0 + a.n_steps;
 }
 
-// flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
-__device__ __forceinline__ float reapply_flips(float v, const GridDev& g, DevCtrl* ctrl, const DevSched& sched,
-                                               long long step, int z, int y, int x) {
-  (void)ctrl;
-  if (!sched.enabled) return v;
-  const long long i = step - sched.t0;
-  if (i < 0 || i >= sched.n) return v;
-  for (int k = sched.off[i]; k < sched.off[i + 1]; ++k) {
-    const DevFlip f = sched.flips[k];
-    if (f.grid == g.gid && f.target == 0 && f.z == z && f.y == y && f.x == x)
-      v = __int_as_float(__float_as_int(v) ^ (1 << (f.bit & 31)));
-  }
-  return v;
-}
-
 // Box (z, y, x ranges) of u^{s+1} points whose stencil read something that the fix
 // f = (kind, z, y, x) of u^s changed.
 __device__ __forceinline__ void fix_box(const GridDev& g, int4 f, int lo[3], int hi[3]) {
@@ -277,7 +262,8 @@ static int check_smem(const GridDev& g, int acc) { return 256 + check_box_bytes(
 //   after the window every thread reduces a slice of the partials into a(F) and compares
 //   with P^d; on a mismatch the window is recomputed from ck without injection (the same
 //   buffers, so the roles stay fixed) and compared again.  Then F becomes the checkpoint.
-// One grid barrier per sweep plus one per window.
+// One grid barrier per sweep plus one per window (a payload barrier that returns the
+// comparison's count of failing entries to every CTA).
 __device__ __forceinline__ void window_buffers(int ck, int& w0, int& w1) {
   w0 = (ck + 1) % 3;
   w1 = (ck + 2) % 3;
@@ -298,6 +284,10 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
   }
   __syncthreads();
   unsigned long long* bar = &g.gc->bar;
+  unsigned long long* bars = g.gc->bars;  // payload barrier of the window comparisons
+  unsigned nbar = 0;
+  __shared__ unsigned s_fails;
+  if (threadIdx.x == 0) s_fails = 0;
   const int ntiles = g.ntx * g.nty;
   const bool resident_c = (int)gridDim.x >= ntiles;
   const bool sweeper = threadIdx.x < kSweepThreads;
@@ -348,10 +338,8 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         ok = grid_barrier(bar, ctrl);
       }
       if (!ok) break;
-      // compare the recomputed checksums of the window's result with the chain
-      if (blockIdx.x == 0 && threadIdx.x == 0) g.gc->fails[attempt] = 0;
-      ok = grid_barrier(bar, ctrl);
-      if (!ok) break;
+      // compare the recomputed checksums of the window's result with the chain; the
+      // count of failing entries rides on the next barrier's arrivals
       const double* pa = g.AP[d & 1];
       const double* pb = g.BP[d & 1];
       unsigned nf = 0;
@@ -370,10 +358,10 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
           note_resid(g, __ldcg(pb + b), sum);
         }
       }
-      if (nf) atomicAdd(&g.gc->fails[attempt], nf);
-      ok = grid_barrier(bar, ctrl);
+      if (nf) atomicAdd(&s_fails, nf);
+      unsigned bad = 0;
+      ok = grid_barrier_sum(bars, nbar++, &s_fails, ctrl, &bad);
       if (!ok) break;
-      const unsigned bad = ld_acquire_u32(&g.gc->fails[attempt]);
       if (bad == 0) break;
       if (attempt == 1) {  // the fault-free recomputation must verify
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctrl, kStUncorrectable);

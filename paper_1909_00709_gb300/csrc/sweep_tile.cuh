@@ -474,6 +474,21 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_u, const CUtens
   sweep_tile_run<TY, PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, sm, seq, pbuf);
 }
 
+// flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
+static __device__ __forceinline__ float reapply_flips(float v, const GridDev& g, DevCtrl* ctrl, const DevSched& sched,
+                                               long long step, int z, int y, int x) {
+  (void)ctrl;
+  if (!sched.enabled) return v;
+  const long long i = step - sched.t0;
+  if (i < 0 || i >= sched.n) return v;
+  for (int k = sched.off[i]; k < sched.off[i + 1]; ++k) {
+    const DevFlip f = sched.flips[k];
+    if (f.grid == g.gid && f.target == 0 && f.z == z && f.y == y && f.x == x)
+      v = __int_as_float(__float_as_int(v) ^ (1 << (f.bit & 31)));
+  }
+  return v;
+}
+
 // ------------------------------------------------- partials, recomputed exactly
 // The same arithmetic, in the same order, as the sweep epilogue above, for one
 // column (a-partial) or one row (b-partial, one full warp) of one tile.  Used when
