@@ -307,8 +307,9 @@ def run_ours(args, rank, world, local):
 
 
 def side_runs(dev, stream, flush):
-    """The precision study (fault-free 512x512x64, three checksum accumulations) and the
-    large 1024x1024x256 grid (unprotected / online / offline), each timed with CUDA events."""
+    """The precision study (fault-free 512x512x64, three checksum accumulations), the
+    boundary rules, the large 1024x1024x256 grid (unprotected / online / offline), many
+    uneven grids, and the paper's campaigns, each timed with CUDA events."""
     import math
     import numpy as np
     import torch
@@ -354,6 +355,21 @@ def side_runs(dev, stream, flush):
         bit = max(0, math.ceil(math.log2(1.25 * eps * top) - e_min + 23))
         prec[name] = {"glups": glups, "max_residual": r, "false_positives": n_ev, "checksum_rel_err": err,
                       "eps_calibrated": eps, "detectable_bit": bit}
+    # boundary rules (Sec. 3.3): clamped, periodic and empty (zero) boundaries on the
+    # L2-resident benchmark grid and on the HBM-bound 512x512x64 grid; offline where the
+    # boundary terms vanish without the grid (clamped with the symmetric HotSpot weights,
+    # periodic)
+    bnd = {}
+    for bname, bcv in (("clamped", abi.BC_CLAMP), ("periodic", abi.BC_PERIODIC), ("zero", abi.BC_ZERO)):
+        for shape, sweeps in ((SHAPE, SWEEPS), (PRECISION_SHAPE, PRECISION_SWEEPS)):
+            r = {}
+            for mname, mode in (("unprotected", abi.MODE_NONE), ("online", abi.MODE_ONLINE),
+                                ("offline", abi.MODE_OFFLINE)):
+                if mode == abi.MODE_OFFLINE and bcv == abi.BC_ZERO:
+                    continue
+                r[mname], _ = timed(shape, mode, sweeps, 6, boundary=bcv)
+            r["overhead_pct"] = {k: (r["unprotected"] / v - 1.0) * 100.0 for k, v in r.items() if k != "unprotected"}
+            bnd.setdefault(bname, {})["x".join(map(str, shape))] = r
     large = {}
     lam = 1e-6 * math.prod(LARGE_SHAPE)  # flips per sweep
     for name, mode, rate in (("unprotected", abi.MODE_NONE, 0.0), ("online", abi.MODE_ONLINE, 0.0),
@@ -454,7 +470,8 @@ def side_runs(dev, stream, flush):
         errs = np.array(errs)
         errcamp[name] = {"median_l2": float(np.median(errs)), "mean_l2": float(np.mean(errs[np.isfinite(errs)])),
                          "share_exact": float(np.mean(errs == 0.0))}
-    return {"batch": batch, "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
+    return {"boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16}, "batch": batch,
+            "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
             "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
                           "variants": prec},
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,

@@ -6,11 +6,13 @@
  * What the library computes, per grid of nx*ny*nz FP32 points u[z][y][x]:
  *   - the sweep of Eq. (1) with the 7-point HotSpot3D set S (centre, x-1, x+1, y-1,
  *     y+1, z-1, z+1) and the constant term C = sdc*P + c_amb*t_amb, with clamped
- *     boundaries (an out-of-range neighbour is the centre, Fig. 2);
+ *     boundaries (an out-of-range neighbour is the centre, Fig. 2), or periodic or
+ *     empty (zero) ones (Sec. 3.3, "Dealing with Boundary Conditions");
  *   - per-plane row and column checksums a[z][x] = sum_y u, b[z][y] = sum_x u
  *     (Eq. 2, 3), fused into the sweep;
  *   - the interpolated checksums of Theorem 1 (Eq. 4, 5; boundary terms alpha, beta
- *     in closed form for the clamped rule), the relative test of Sec. 3.4, location
+ *     in closed form for each boundary rule; zero for the periodic one, which gives
+ *     the simple form of Eq. 6, 7), the relative test of Sec. 3.4, location
  *     at the intersection of the failing row and column, and the correction of
  *     Eq. (8) / Fig. 9, every sweep (online mode, Sec. 3);
  *   - the offline mode of Sec. 4: a checkpoint every Delta sweeps, Theorem 1 chained
@@ -71,6 +73,14 @@ typedef enum {
   ABFT_ACC_FP64 = 2      /* FP64 accumulation from the first add */
 } abft_acc;
 
+/* Boundary rule of Eq. (1) for a neighbour outside the grid, on every axis (Sec. 3.3,
+   "Dealing with Boundary Conditions"). */
+typedef enum {
+  ABFT_BC_CLAMP = 0,     /* the centre point (Fig. 2) */
+  ABFT_BC_PERIODIC = 1,  /* the point on the opposite face; alpha = beta = 0 in Theorem 1 */
+  ABFT_BC_ZERO = 2       /* zero ("empty" boundaries) */
+} abft_boundary;
+
 typedef enum {
   ABFT_EV_CORRECTED = 1,  /* Eq. (8) applied at (z, y, x); before/after hold the values */
   ABFT_EV_RECOMPUTED = 2, /* a flagged line recomputed from u^t: row y (x = -1) or column x (y = -1) */
@@ -102,7 +112,8 @@ typedef struct {
                                that pass (abft_counters.max_residual); costs one atomic per entry */
   int32_t depth;            /* temporal blocking: unprotected sweeps (mode NONE, and the sweeps of
                                an offline window before its last) advance `depth` (1..4) sweeps per
-                               pass over the grid where a grid is swept launch by launch; 1 = off */
+                               pass over the grid where a grid is swept launch by launch; 1 = off.
+                               Used with the clamped boundary only (others sweep one at a time). */
   int32_t overlap;          /* 1: a single grid checked online launch by launch (too large for the
                                persistent kernel) runs each sweep's check beside the next sweep and
                                recomputes that sweep only when the check corrected something */
@@ -110,6 +121,7 @@ typedef struct {
                                launch per tile class and one check launch per sweep (CUDA graphs
                                of graph_steps sweeps); 0: grid by grid. Offline steps always go
                                grid by grid. */
+  int32_t boundary;         /* abft_boundary of every grid of the context */
   void* stream;             /* cudaStream_t used for all device work */
 } abft_options;
 
@@ -137,7 +149,7 @@ typedef struct {
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
    sweeps, default tile, 64 flips per step, persistent launches, whole-column tiles for
    shallow grids, no residual tracking, depth 1, overlapped checks, batched launches,
-   NULL stream. */
+   clamped boundaries, NULL stream. */
 ABFT_API void abft_default_options(abft_options* opt);
 
 /* Bytes of device workspace abft_init needs for these grids and options
@@ -161,8 +173,9 @@ ABFT_API abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n
 /* Advance every grid by n sweeps in the given mode (abft_mode).  ONLINE checks and
    corrects after each sweep (Sec. 3.2-3.5).  OFFLINE runs windows of Delta sweeps
    (the last one may be shorter), compares once per window and recomputes a
-   window from its checkpoint on a mismatch (Sec. 4); it needs cn == cs and
-   cw == ce (the boundary terms vanish) and returns ABFT_E_INVAL otherwise.
+   window from its checkpoint on a mismatch (Sec. 4); it needs boundary terms that
+   vanish (periodic boundaries, or clamped ones with cn == cs and cw == ce) and
+   returns ABFT_E_INVAL otherwise.
    Synchronises the stream at the end.  Errors: ABFT_E_INVAL, ABFT_E_CUDA,
    ABFT_E_TIMEOUT, ABFT_E_UNCORRECTABLE, ABFT_E_TRUNCATED (events dropped; the
    sweeps still completed). */

@@ -16,6 +16,7 @@ from . import build as _build
 
 MODE_NONE, MODE_ONLINE, MODE_OFFLINE = 0, 1, 2
 ACC_FP32, ACC_TWOSUM, ACC_FP64 = 0, 1, 2
+BC_CLAMP, BC_PERIODIC, BC_ZERO = 0, 1, 2
 EV_CORRECTED, EV_RECOMPUTED, EV_ROLLBACK = 1, 2, 3
 KERNEL_KINDS = ("sweep_plain", "sweep_protected", "check_online", "check_offline", "chain", "other",
                 "persistent_plain", "persistent_protected")
@@ -43,7 +44,7 @@ class abft_options(ct.Structure):
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
                 ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("overlap", ct.c_int32),
-                ("batch", ct.c_int32),
+                ("batch", ct.c_int32), ("boundary", ct.c_int32),
                 ("stream", ct.c_void_p)]
 
 

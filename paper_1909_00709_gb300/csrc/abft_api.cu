@@ -74,7 +74,8 @@ bool valid_options(const abft_options& o) {
          o.max_flips_per_step <= 511 && (o.tile_y == 0 || o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32) &&
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
          (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1) &&
-         o.depth >= 1 && o.depth <= 4 && (o.overlap == 0 || o.overlap == 1);
+         o.depth >= 1 && o.depth <= 4 && (o.overlap == 0 || o.overlap == 1) && o.boundary >= ABFT_BC_CLAMP &&
+         o.boundary <= ABFT_BC_ZERO;
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -394,7 +395,12 @@ int other_than(int a, int b) {
   return -1;
 }
 
-bool offline_capable(const abft_coeffs& c) { return c.cn == c.cs && c.cw == c.ce; }
+// Theorem 1 without the grid (the chain of Fig. 10) needs vanishing boundary terms:
+// always for periodic boundaries, for clamped ones when opposite in-plane weights are
+// equal, never for empty ones (their terms hold the edge rows themselves)
+bool offline_capable(const abft_coeffs& c, int bc) {
+  return bc == ABFT_BC_PERIODIC || (bc == ABFT_BC_CLAMP && c.cn == c.cs && c.cw == c.ce);
+}
 
 // upload the flips of sweeps [t0, t0 + n) (n <= kSchedSteps); returns the number of
 // sweeps actually covered (less than n when the capacity runs out)
@@ -739,7 +745,9 @@ cudaError_t batch_sweep(abft_ctx* ctx, const Launch& L, bool prot, bool counted)
     const BatchArgs a = batch_args(ctx, b);
     Launch Lc = L;
     if (fork && c > 0) Lc.s = ctx->side_stream;
-    auto f = [&] { return launch_sweep_batch(Lc, a, b.blocks, b.smem, b.shallow, b.ty, prot, acc); };
+    auto f = [&] {
+      return launch_sweep_batch(Lc, a, b.blocks, b.smem, b.shallow, b.ty, prot, acc, ctx->opt.boundary);
+    };
     const cudaError_t e = counted ? run(ctx, prot ? kKSweepProt : kKSweepPlain, f) : f();
     if (e != cudaSuccess) return e;
   }
@@ -785,7 +793,7 @@ abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
       abft_status s = ensure_checksums(ctx, gi);
       if (s) return s;
     }
-  for (const auto& b : ctx->bcls) CK(batch_prepare(b.shallow, b.ty, prot, ctx->opt.acc, b.smem));
+  for (const auto& b : ctx->bcls) CK(batch_prepare(b.shallow, b.ty, prot, ctx->opt.acc, ctx->opt.boundary, b.smem));
   if (prot && ctx->bchk.box) CK(batch_check_prepare(ctx->opt.acc, ctx->bchk.smem));
   if (ctx->roles_pending) CK(cudaEventSynchronize(ctx->roles_ev));  // the previous upload has been read
   for (int gi = 0; gi < ctx->n; ++gi) {
@@ -1022,6 +1030,7 @@ void abft_default_options(abft_options* o) {
   o->max_flips_per_step = 64;
   o->persistent = 1;
   o->shallow = 1;
+  o->boundary = ABFT_BC_CLAMP;
   o->stream = nullptr;
 }
 
@@ -1109,6 +1118,9 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   };
   if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(ABFT_E_CUDA);
   ctx->opt = *opt;
+  // temporal blocking recomputes halo cells level by level, which the clamped rule
+  // allows locally; other boundaries sweep one level at a time
+  if (opt->boundary != ABFT_BC_CLAMP) ctx->opt.depth = 1;
   ctx->stream = (cudaStream_t)opt->stream;
   ctx->n = n_grids;
   ctx->grids.assign(grids, grids + n_grids);
@@ -1151,6 +1163,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.pb_stride = (int)align_up(G.ny, 4);
     g.acc = opt->acc;
     g.gid = i;
+    g.bc = opt->boundary;
     g.eps = opt->eps;
     const abft_coeffs& c = coeffs[i];
     g.k = Coef{c.cc, c.cw, c.ce, c.cn, c.cs, c.cb, c.ct};
@@ -1204,8 +1217,8 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     char e[256];
     if (make_tensor_maps(g, g.ty, &ctx->tm_u[3 * i], &ctx->tm_c[i], e, sizeof e) != cudaSuccess ||
         make_partial_maps(g, &ctx->tm_p[4 * i], e, sizeof e) != cudaSuccess ||
-        (opt->depth >= 2 &&
-         make_tb_maps(g, opt->depth, &ctx->tm_tb[4 * i], &ctx->tm_tb[4 * i + 3], e, sizeof e) != cudaSuccess)) {
+        (ctx->opt.depth >= 2 &&
+         make_tb_maps(g, ctx->opt.depth, &ctx->tm_tb[4 * i], &ctx->tm_tb[4 * i + 3], e, sizeof e) != cudaSuccess)) {
       st = fail(ctx, ABFT_E_CUDA, "%s", e);
       return bail(st);
     }
@@ -1260,8 +1273,10 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
   if (ctx->status_seen & kStTimeout) return fail(ctx, ABFT_E_TIMEOUT, "context poisoned by an earlier timeout");
   if (mode == ABFT_MODE_OFFLINE)
     for (int gi = 0; gi < ctx->n; ++gi)
-      if (!offline_capable(ctx->co[gi]))
-        return fail(ctx, ABFT_E_INVAL, "offline mode needs cn == cs and cw == ce (grid %d)", gi);
+      if (!offline_capable(ctx->co[gi], ctx->opt.boundary))
+        return fail(ctx, ABFT_E_INVAL,
+                    "offline mode needs vanishing boundary terms: periodic, or clamped with cn == cs and cw == ce "
+                    "(grid %d)", gi);
   ctx->verified = false;
   const int64_t t_end = ctx->step + n;
   abft_status s = ABFT_OK;
@@ -1341,8 +1356,8 @@ abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
     const int c = ctx->cur[gi], r = ctx->ref[gi];
     const int64_t d = ctx->step - ctx->ref_step[gi];
     ctx->v_dist[gi] = d;
-    if (d > 0 && !offline_capable(ctx->co[gi]))
-      return fail(ctx, ABFT_E_INVAL, "chained verification needs cn == cs and cw == ce (grid %d)", gi);
+    if (d > 0 && !offline_capable(ctx->co[gi], ctx->opt.boundary))
+      return fail(ctx, ABFT_E_INVAL, "chained verification needs vanishing boundary terms (grid %d)", gi);
     CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.AP[2], g.BP[2]); }));
     const double* pa = g.A[r];
     const double* pb = g.B[r];

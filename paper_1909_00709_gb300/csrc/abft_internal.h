@@ -75,6 +75,7 @@ struct GridDev {
   int shallow;              // 1: whole-column tiles (all nz planes staged at once)
   int track;                // 1: keep the running maximum of the passing residuals
   int gid;
+  int bc;                   // abft_boundary: what a neighbour outside the grid reads
   Coef k;
   double eps;
   float* u[3];              // state buffers
@@ -194,9 +195,10 @@ struct BatchArgs {
 };
 constexpr int kBatchRounds = 16;  // 32-entry check rounds per block of the batched check (2 per warp)
 int batch_sweep_smem(int shallow, int ty, int nz);
-cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int smem);
+// bc: the grids' abft_boundary (one rule per context)
+cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int bc, int smem);
 cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, int smem, int shallow, int ty,
-                               bool prot, int acc);
+                               bool prot, int acc, int bc);
 // box > 0: the partials come in TMA boxes of `box` bytes, nw warps per block, `smem`
 // bytes of dynamic shared memory; box == 0: plain loads, 8 warps per block
 cudaError_t launch_check_batch(const Launch& L, const BatchArgs& a, int blocks, int acc, int box, int nw, int smem);

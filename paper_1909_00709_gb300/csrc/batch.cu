@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
   const CUtensorMap* tm_u = a.tm + kBatchMaps * gi + in;
   const CUtensorMap* tm_c = a.tm + kBatchMaps * gi + 3;
   float* uout = pick3(g.u[0], g.u[1], g.u[2], out);
+  const float* uin = pick3(g.u[0], g.u[1], g.u[2], in);
   Tiles tiles;
   tiles.setup(smem_raw, g.nz);
   if (threadIdx.x == 0) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
   __syncthreads();
   const int txi = t % g.ntx, tyi = t / g.ntx;
   tiles.issue(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, true);
-  tiles.template run<PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, 0);
+  tiles.template run<PROT, ACC>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, 0);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
@@ -200,29 +201,36 @@ static cudaError_t dispatch_acc(bool prep, const Launch* L, const BatchArgs* a, 
   }
 }
 
-static cudaError_t dispatch(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
-                            bool prot, int acc) {
+template <bool CL>
+static cudaError_t dispatch_cl(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
+                               bool prot, int acc) {
   if (shallow) {
-    if (ty == 16) return dispatch_acc<ShallowTiles<16>>(prep, L, a, blocks, smem, prot, acc);
-    if (ty == 8) return dispatch_acc<ShallowTiles<8>>(prep, L, a, blocks, smem, prot, acc);
+    if (ty == 16) return dispatch_acc<ShallowTiles<16, CL>>(prep, L, a, blocks, smem, prot, acc);
+    if (ty == 8) return dispatch_acc<ShallowTiles<8, CL>>(prep, L, a, blocks, smem, prot, acc);
     return cudaErrorInvalidValue;
   }
   switch (ty) {
-    case 8: return dispatch_acc<StreamTiles<8>>(prep, L, a, blocks, smem, prot, acc);
-    case 16: return dispatch_acc<StreamTiles<16>>(prep, L, a, blocks, smem, prot, acc);
-    case 32: return dispatch_acc<StreamTiles<32>>(prep, L, a, blocks, smem, prot, acc);
+    case 8: return dispatch_acc<StreamTiles<8, CL>>(prep, L, a, blocks, smem, prot, acc);
+    case 16: return dispatch_acc<StreamTiles<16, CL>>(prep, L, a, blocks, smem, prot, acc);
+    case 32: return dispatch_acc<StreamTiles<32, CL>>(prep, L, a, blocks, smem, prot, acc);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int smem) {
-  return dispatch(true, nullptr, nullptr, 0, smem, shallow, ty, prot, acc);
+static cudaError_t dispatch(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
+                            bool prot, int acc, int bc) {
+  return bc == ABFT_BC_CLAMP ? dispatch_cl<true>(prep, L, a, blocks, smem, shallow, ty, prot, acc)
+                             : dispatch_cl<false>(prep, L, a, blocks, smem, shallow, ty, prot, acc);
+}
+
+cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int bc, int smem) {
+  return dispatch(true, nullptr, nullptr, 0, smem, shallow, ty, prot, acc, bc);
 }
 
 cudaError_t launch_sweep_batch(const Launch& L, const BatchArgs& a, int blocks, int smem, int shallow, int ty,
-                               bool prot, int acc) {
+                               bool prot, int acc, int bc) {
   if (blocks <= 0) return cudaSuccess;
-  return dispatch(false, &L, &a, blocks, smem, shallow, ty, prot, acc);
+  return dispatch(false, &L, &a, blocks, smem, shallow, ty, prot, acc, bc);
 }
 
 template <int ACC>

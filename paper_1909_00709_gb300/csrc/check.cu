@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kCheckThreads)
       resolve_plane(sm, g, g.u[in], g.u[out], g.A[out], g.B[out], g.AP[0], g.BP[0], step, ctrl, ev,
                     &g.gc->unresolved, z);
       // u[out] changed: a next sweep already started is stale in every tile whose
-      // stencil read a changed point (tiles span all planes, so only x and y matter)
+      // stencil read a changed point (with periodic boundaries a fix on a face also
+      // reaches the opposite face: every tile row or column, or every plane)
       if (threadIdx.x == 0) {
         const int ntiles = g.ntx * g.nty;
         int* hi1 = g.tdirty;            // highest marked plane + 1
@@ -77,13 +78,16 @@ __global__ void __launch_bounds__(kCheckThreads)
         const bool every = sm.nfix > kFixCap;  // the list overflowed: the whole plane
         for (int k = 0; k < (every ? 1 : sm.nfix); ++k) {
           const int4 f = every ? make_int4(kFixPlane, z, -1, -1) : sm.fix[k];  // (kind, z, y, x)
-          const bool all_y = f.x == kFixPlane || f.x == kFixCol, all_x = f.x == kFixPlane || f.x == kFixRow;
+          const bool wrap = g.bc == ABFT_BC_PERIODIC;
+          const bool all_y = f.x == kFixPlane || f.x == kFixCol || (wrap && (f.z == 0 || f.z == g.ny - 1));
+          const bool all_x = f.x == kFixPlane || f.x == kFixRow || (wrap && (f.w == 0 || f.w == g.nx - 1));
+          const bool all_z = wrap && (f.y == 0 || f.y == g.nz - 1);
           const int y0 = all_y ? 0 : max(f.z - 1, 0) / g.ty, y1 = all_y ? g.nty - 1 : min(f.z + 1, g.ny - 1) / g.ty;
           const int x0 = all_x ? 0 : max(f.w - 1, 0) / kTX, x1 = all_x ? g.ntx - 1 : min(f.w + 1, g.nx - 1) / kTX;
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx) {
-              atomicMax(&hi1[ty * g.ntx + tx], f.y + 1);
-              atomicMax(&lorev[ty * g.ntx + tx], g.nz - f.y);
+              atomicMax(&hi1[ty * g.ntx + tx], all_z ? g.nz : f.y + 1);
+              atomicMax(&lorev[ty * g.ntx + tx], all_z ? g.nz : g.nz - f.y);
             }
         }
         sm.nfix = 0;

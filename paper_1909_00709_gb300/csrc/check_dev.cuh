@@ -93,13 +93,13 @@ __device__ __forceinline__ double reduce_b(const GridDev& g, int z, int y, int p
   return sum_partials<ACC>(pbuf ? g.PB2 : g.PB, (size_t)z * g.pb_stride + y, (size_t)g.nz * g.pb_stride, g.ntx);
 }
 
-// Theorem 1 for the clamped 7-point set (Eq. 4 for a, Eq. 5 for b): shifts along the
-// surviving in-plane axis and along z are clamped index shifts of the vector; the two
-// shifts along the collapsed axis add the entry to itself plus the boundary term
-// (w_- - w_+) * (u at the first minus u at the last index), zero for equal weights.
+// Theorem 1 for the 7-point set (Eq. 4 for a, Eq. 5 for b): shifts along the surviving
+// in-plane axis and along z are shifts of the vector under the boundary rule (clamped
+// index, wrapped index, or zero outside); the two shifts along the collapsed axis add
+// the entry to itself plus the boundary term alpha/beta (edge_of).
 // Evaluated with explicit FP64 roundings in a fixed order: c the checksum of C, v0 the
-// entry, v1/v2 its clamped neighbours along the surviving in-plane axis, v3/v4 along z,
-// w0 the summed weight of the centre and the collapsed-axis pair.
+// entry, v1/v2 its neighbours along the surviving in-plane axis, v3/v4 along z, w0 the
+// summed weight of the centre and the collapsed-axis pair.
 __device__ __forceinline__ double interp(double c, double v0, double v1, double v2, double v3, double v4,
                                          double w0, double w1, double w2, double w3, double w4, double edge) {
   double p = __fma_rn(w0, v0, c);
@@ -118,33 +118,54 @@ __device__ __forceinline__ double edge_term(float wm, float wp, float first, flo
   return __dmul_rn(__dadd_rn((double)wm, -(double)wp), __dadd_rn((double)first, -(double)last));
 }
 
+// The boundary term along the collapsed axis for its weights wm (shift -1) and wp
+// (shift +1), from u at the first and last index of that axis.  The shifted sums are
+// the checksum plus (ghost before the first index - last) for wm and (ghost after the
+// last index - first) for wp:
+//   clamped (ghosts first, last): (wm - wp)(first - last)
+//   periodic (ghosts last, first): 0
+//   empty (ghosts 0): -(wm last + wp first), both products exact in FP64
+__device__ __forceinline__ bool edge_needed(int bc, float wm, float wp) {
+  return bc == ABFT_BC_CLAMP ? wm != wp : (bc == ABFT_BC_ZERO && (wm != 0.f || wp != 0.f));
+}
+__device__ __forceinline__ double edge_of(int bc, float wm, float wp, float first, float last) {
+  if (bc == ABFT_BC_CLAMP) return edge_term(wm, wp, first, last);
+  if (bc == ABFT_BC_PERIODIC) return 0.0;
+  return __dadd_rn(-__dmul_rn((double)wm, (double)last), -__dmul_rn((double)wp, (double)first));
+}
+
+// entry (z, i) of a vector with `len` entries per plane; zero outside (index -1)
+__device__ __forceinline__ double ld_entry(const double* V, int z, int i, int len) {
+  return (z < 0 || i < 0) ? 0.0 : __ldcg(V + (size_t)z * len + i);
+}
+
 __device__ __forceinline__ double predict_a(const GridDev& g, const double* A, const float* u, int z, int x) {
   const int nx = g.nx;
-  const int xm = x > 0 ? x - 1 : 0, xp = x < nx - 1 ? x + 1 : nx - 1;
-  const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+  const int xm = nb_index(x, -1, nx, g.bc), xp = nb_index(x, 1, nx, g.bc);
+  const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
   const Coef& k = g.k;
   double edge = 0.0;
-  if (u != nullptr && k.cn != k.cs) {
+  if (u != nullptr && edge_needed(g.bc, k.cn, k.cs)) {
     const size_t pl = (size_t)z * g.ny * g.px;
-    edge = edge_term(k.cn, k.cs, __ldcg(u + pl + x), __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + x));
+    edge = edge_of(g.bc, k.cn, k.cs, __ldcg(u + pl + x), __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + x));
   }
-  return interp(g.cx[(size_t)z * nx + x], __ldcg(A + (size_t)z * nx + x), __ldcg(A + (size_t)z * nx + xm),
-                __ldcg(A + (size_t)z * nx + xp), __ldcg(A + (size_t)zm * nx + x), __ldcg(A + (size_t)zp * nx + x),
+  return interp(g.cx[(size_t)z * nx + x], __ldcg(A + (size_t)z * nx + x), ld_entry(A, z, xm, nx),
+                ld_entry(A, z, xp, nx), ld_entry(A, zm, x, nx), ld_entry(A, zp, x, nx),
                 weight_sum3(k.cc, k.cn, k.cs), k.cw, k.ce, k.cb, k.ct, edge);
 }
 
 __device__ __forceinline__ double predict_b(const GridDev& g, const double* B, const float* u, int z, int y) {
   const int ny = g.ny;
-  const int ym = y > 0 ? y - 1 : 0, yp = y < ny - 1 ? y + 1 : ny - 1;
-  const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+  const int ym = nb_index(y, -1, ny, g.bc), yp = nb_index(y, 1, ny, g.bc);
+  const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
   const Coef& k = g.k;
   double edge = 0.0;
-  if (u != nullptr && k.cw != k.ce) {
+  if (u != nullptr && edge_needed(g.bc, k.cw, k.ce)) {
     const size_t row = ((size_t)z * g.ny + y) * g.px;
-    edge = edge_term(k.cw, k.ce, __ldcg(u + row), __ldcg(u + row + g.nx - 1));
+    edge = edge_of(g.bc, k.cw, k.ce, __ldcg(u + row), __ldcg(u + row + g.nx - 1));
   }
-  return interp(g.cy[(size_t)z * ny + y], __ldcg(B + (size_t)z * ny + y), __ldcg(B + (size_t)z * ny + ym),
-                __ldcg(B + (size_t)z * ny + yp), __ldcg(B + (size_t)zm * ny + y), __ldcg(B + (size_t)zp * ny + y),
+  return interp(g.cy[(size_t)z * ny + y], __ldcg(B + (size_t)z * ny + y), ld_entry(B, z, ym, ny),
+                ld_entry(B, z, yp, ny), ld_entry(B, zm, y, ny), ld_entry(B, zp, y, ny),
                 weight_sum3(k.cc, k.cw, k.ce), k.cn, k.cs, k.cb, k.ct, edge);
 }
 
@@ -409,18 +430,19 @@ __device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, i
     idx = e - z * g.nx;
     which = 0;
     const int x = idx, nx = g.nx;
-    const int xm = x > 0 ? x - 1 : 0, xp = x < nx - 1 ? x + 1 : nx - 1;
-    const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+    const int xm = nb_index(x, -1, nx, g.bc), xp = nb_index(x, 1, nx, g.bc);
+    const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
     const double* A = g.A[in];
     c = g.cx[(size_t)z * nx + x];
     v0 = __ldcg(A + (size_t)z * nx + x);
-    v1 = __ldcg(A + (size_t)z * nx + xm);
-    v2 = __ldcg(A + (size_t)z * nx + xp);
-    v3 = __ldcg(A + (size_t)zm * nx + x);
-    v4 = __ldcg(A + (size_t)zp * nx + x);
-    if (k.cn != k.cs) {
+    v1 = ld_entry(A, z, xm, nx);
+    v2 = ld_entry(A, z, xp, nx);
+    v3 = ld_entry(A, zm, x, nx);
+    v4 = ld_entry(A, zp, x, nx);
+    if (edge_needed(g.bc, k.cn, k.cs)) {
       const size_t pl = (size_t)z * g.ny * g.px;
-      edge = edge_term(k.cn, k.cs, __ldcg(g.u[in] + pl + x), __ldcg(g.u[in] + pl + (size_t)(g.ny - 1) * g.px + x));
+      edge = edge_of(g.bc, k.cn, k.cs, __ldcg(g.u[in] + pl + x),
+                     __ldcg(g.u[in] + pl + (size_t)(g.ny - 1) * g.px + x));
     }
     P = g.PA;
     i0 = (size_t)z * g.pa_stride + x;
@@ -432,18 +454,18 @@ __device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, i
     idx = b - z * g.ny;
     which = 1;
     const int y = idx, ny = g.ny;
-    const int ym = y > 0 ? y - 1 : 0, yp = y < ny - 1 ? y + 1 : ny - 1;
-    const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+    const int ym = nb_index(y, -1, ny, g.bc), yp = nb_index(y, 1, ny, g.bc);
+    const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
     const double* B = g.B[in];
     c = g.cy[(size_t)z * ny + y];
     v0 = __ldcg(B + (size_t)z * ny + y);
-    v1 = __ldcg(B + (size_t)z * ny + ym);
-    v2 = __ldcg(B + (size_t)z * ny + yp);
-    v3 = __ldcg(B + (size_t)zm * ny + y);
-    v4 = __ldcg(B + (size_t)zp * ny + y);
-    if (k.cw != k.ce) {
+    v1 = ld_entry(B, z, ym, ny);
+    v2 = ld_entry(B, z, yp, ny);
+    v3 = ld_entry(B, zm, y, ny);
+    v4 = ld_entry(B, zp, y, ny);
+    if (edge_needed(g.bc, k.cw, k.ce)) {
       const size_t row = ((size_t)z * g.ny + y) * g.px;
-      edge = edge_term(k.cw, k.ce, __ldcg(g.u[in] + row), __ldcg(g.u[in] + row + g.nx - 1));
+      edge = edge_of(g.bc, k.cw, k.ce, __ldcg(g.u[in] + row), __ldcg(g.u[in] + row + g.nx - 1));
     }
     P = g.PB;
     i0 = (size_t)z * g.pb_stride + y;
@@ -542,20 +564,20 @@ __device__ __forceinline__ void check_box_round(const GridDev& g, const InterpW&
   const int idx = c + lane;
   const bool live = idx < len;
   // interpolation inputs while the box is in flight
-  const int im = idx > 0 ? idx - 1 : 0, ip = idx < len - 1 ? idx + 1 : len - 1;
-  const int zm = z > 0 ? z - 1 : 0, zp = z < g.nz - 1 ? z + 1 : g.nz - 1;
+  const int im = nb_index(idx, -1, len, g.bc), ip = nb_index(idx, 1, len, g.bc);
+  const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
   const double* V = is_a ? g.A[in] : g.B[in];
   const double* CC = is_a ? g.cx : g.cy;
   const Coef& k = g.k;
-  const bool asym = is_a ? k.cn != k.cs : k.cw != k.ce;
+  const bool asym = is_a ? edge_needed(g.bc, k.cn, k.cs) : edge_needed(g.bc, k.cw, k.ce);
   double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, cc = 0;
   float ef = 0.f, el = 0.f;
   if (live) {
     v0 = __ldcg(V + (size_t)z * len + idx);
-    v1 = __ldcg(V + (size_t)z * len + im);
-    v2 = __ldcg(V + (size_t)z * len + ip);
-    v3 = __ldcg(V + (size_t)zm * len + idx);
-    v4 = __ldcg(V + (size_t)zp * len + idx);
+    v1 = ld_entry(V, z, im, len);
+    v2 = ld_entry(V, z, ip, len);
+    v3 = ld_entry(V, zm, idx, len);
+    v4 = ld_entry(V, zp, idx, len);
     cc = CC[(size_t)z * len + idx];
     if (asym) {
       const float* u = g.u[in];
@@ -591,12 +613,12 @@ __device__ __forceinline__ void check_box_round(const GridDev& g, const InterpW&
   const double s = t[0].total<ACC>();
   double p;
   if (is_a) {
-    const double edge = asym ? edge_term(k.cn, k.cs, ef, el) : 0.0;
+    const double edge = asym ? edge_of(g.bc, k.cn, k.cs, ef, el) : 0.0;
     p = interp(cc, v0, v1, v2, v3, v4, w.a0, w.cw, w.ce, w.cb, w.ct, edge);
     g.A[out][(size_t)z * len + idx] = s;
     g.AP[0][(size_t)z * len + idx] = p;
   } else {
-    const double edge = asym ? edge_term(k.cw, k.ce, ef, el) : 0.0;
+    const double edge = asym ? edge_of(g.bc, k.cw, k.ce, ef, el) : 0.0;
     p = interp(cc, v0, v1, v2, v3, v4, w.b0, w.cn, w.cs, w.cb, w.ct, edge);
     g.B[out][(size_t)z * len + idx] = s;
     g.BP[0][(size_t)z * len + idx] = p;

@@ -20,20 +20,34 @@ __device__ __forceinline__ float hs_update(const Coef& k, float c, float w, floa
   return v;
 }
 
-// Eq. (1) at one point read straight from global memory, neighbours clamped (Fig. 2).
+// Eq. (1) at one point read straight from global memory.  A neighbour outside the grid
+// follows the boundary rule: the centre (clamped, Fig. 2), the point on the opposite
+// face (periodic) or zero (empty boundaries, Sec. 3.3).
 __device__ __forceinline__ float point_update(const GridDev& g, const float* __restrict__ u,
                                               int z, int y, int x) {
   const size_t plane = (size_t)g.ny * g.px;
   const float* p = u + (size_t)z * plane + (size_t)y * g.px + x;
   const float c = __ldcg(p);
-  const float w = x > 0 ? __ldcg(p - 1) : c;
-  const float e = x < g.nx - 1 ? __ldcg(p + 1) : c;
-  const float n = y > 0 ? __ldcg(p - g.px) : c;
-  const float s = y < g.ny - 1 ? __ldcg(p + g.px) : c;
-  const float b = z > 0 ? __ldcg(p - (ptrdiff_t)plane) : c;
-  const float t = z < g.nz - 1 ? __ldcg(p + plane) : c;
+  // outside: clamped -> c, periodic -> the wrapped point at offset `wrap`, empty -> 0
+  auto edge = [&](ptrdiff_t wrap) -> float {
+    return g.bc == ABFT_BC_CLAMP ? c : (g.bc == ABFT_BC_PERIODIC ? __ldcg(p + wrap) : 0.f);
+  };
+  const float w = x > 0 ? __ldcg(p - 1) : edge(g.nx - 1);
+  const float e = x < g.nx - 1 ? __ldcg(p + 1) : edge(-(ptrdiff_t)(g.nx - 1));
+  const float n = y > 0 ? __ldcg(p - g.px) : edge((ptrdiff_t)(g.ny - 1) * g.px);
+  const float s = y < g.ny - 1 ? __ldcg(p + g.px) : edge(-(ptrdiff_t)(g.ny - 1) * g.px);
+  const float b = z > 0 ? __ldcg(p - (ptrdiff_t)plane) : edge((ptrdiff_t)(g.nz - 1) * (ptrdiff_t)plane);
+  const float t = z < g.nz - 1 ? __ldcg(p + plane) : edge(-(ptrdiff_t)(g.nz - 1) * (ptrdiff_t)plane);
   const float C = g.C[(size_t)z * plane + (size_t)y * g.px + x];
   return hs_update(g.k, c, w, e, n, s, b, t, C);
+}
+
+// Index of entry i + d (d = -1 or +1) of a length-n vector or axis under the boundary
+// rule: clamped to i, wrapped, or -1 for "outside, reads zero".
+__device__ __forceinline__ int nb_index(int i, int d, int n, int bc) {
+  const int j = i + d;
+  if (j >= 0 && j < n) return j;
+  return bc == ABFT_BC_CLAMP ? i : (bc == ABFT_BC_PERIODIC ? (j < 0 ? n - 1 : 0) : -1);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

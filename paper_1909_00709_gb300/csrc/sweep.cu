@@ -25,7 +25,8 @@ namespace abft {
 template <class Tiles, bool PROT, int ACC>
 __global__ void __launch_bounds__(256, 2)
     k_sweep(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c,
-            const GridDev g, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
+            const GridDev g, const float* __restrict__ uin, float* __restrict__ uout, DevCtrl* __restrict__ ctrl,
+            DevSched sched) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   sched.load(ctrl);
   Tiles tiles;
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256, 2)
   const long long step = g.gc->step;
   const int txi = blockIdx.x % g.ntx, tyi = blockIdx.x / g.ntx;
   tiles.issue(&tm_u, &tm_c, g, txi, tyi, step, ctrl, sched, true);
-  tiles.template run<PROT, ACC>(&tm_u, &tm_c, g, uout, txi, tyi, ctrl, 0);
+  tiles.template run<PROT, ACC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256, 2)
       }
       __syncthreads();
       tiles.issue(&tm_u, &tm_c, g, txi, tyi, step, ctrl, sched, true);
-      tiles.template run<true, ACC>(&tm_u, &tm_c, g, uout, txi, tyi, ctrl, 0);
+      tiles.template run<true, ACC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
     } else {
       const int ncol = min(kTX, g.nx - x0), nrow = min(TY, g.ny - y0);
       // this sweep's flips inside the tile, gathered once
@@ -152,42 +153,48 @@ int sweep_smem_bytes(int ty, bool) {
 
 template <class Tiles, bool PROT, int ACC>
 static cudaError_t launch_t(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                            int out) {
+                            int in, int out) {
   auto kern = k_sweep<Tiles, PROT, ACC>;
   const int smem = Tiles::smem_bytes(g.nz);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[out], L.ctrl, L.sched);
+  kern<<<g.ntx * g.nty, 256, smem, L.s>>>(tm_in, tm_c, g, g.u[in], g.u[out], L.ctrl, L.sched);
   return cudaGetLastError();
 }
 
 template <class Tiles>
 static cudaError_t launch_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                                int out, bool prot) {
-  if (!prot) return launch_t<Tiles, false, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out);
+                                int in, int out, bool prot) {
+  if (!prot) return launch_t<Tiles, false, ABFT_ACC_FP32>(L, g, tm_in, tm_c, in, out);
   switch (g.acc) {
-    case ABFT_ACC_TWOSUM: return launch_t<Tiles, true, ABFT_ACC_TWOSUM>(L, g, tm_in, tm_c, out);
-    case ABFT_ACC_FP64: return launch_t<Tiles, true, ABFT_ACC_FP64>(L, g, tm_in, tm_c, out);
-    default: return launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, out);
+    case ABFT_ACC_TWOSUM: return launch_t<Tiles, true, ABFT_ACC_TWOSUM>(L, g, tm_in, tm_c, in, out);
+    case ABFT_ACC_FP64: return launch_t<Tiles, true, ABFT_ACC_FP64>(L, g, tm_in, tm_c, in, out);
+    default: return launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, in, out);
+  }
+}
+
+template <bool CL>
+static cudaError_t launch_sweep_cl(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
+                                   const CUtensorMap& tm_c, int in, int out, bool prot) {
+  if (g.shallow) {
+    switch (g.ty) {
+      case 8: return launch_tiles<ShallowTiles<8, CL>>(L, g, tm_in, tm_c, in, out, prot);
+      case 16: return launch_tiles<ShallowTiles<16, CL>>(L, g, tm_in, tm_c, in, out, prot);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (g.ty) {
+    case 8: return launch_tiles<StreamTiles<8, CL>>(L, g, tm_in, tm_c, in, out, prot);
+    case 16: return launch_tiles<StreamTiles<16, CL>>(L, g, tm_in, tm_c, in, out, prot);
+    case 32: return launch_tiles<StreamTiles<32, CL>>(L, g, tm_in, tm_c, in, out, prot);
+    default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c, int in,
                          int out, bool prot) {
-  (void)in;
-  if (g.shallow) {
-    switch (g.ty) {
-      case 8: return launch_tiles<ShallowTiles<8>>(L, g, tm_in, tm_c, out, prot);
-      case 16: return launch_tiles<ShallowTiles<16>>(L, g, tm_in, tm_c, out, prot);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (g.ty) {
-    case 8: return launch_tiles<StreamTiles<8>>(L, g, tm_in, tm_c, out, prot);
-    case 16: return launch_tiles<StreamTiles<16>>(L, g, tm_in, tm_c, out, prot);
-    case 32: return launch_tiles<StreamTiles<32>>(L, g, tm_in, tm_c, out, prot);
-    default: return cudaErrorInvalidValue;
-  }
+  return g.bc == ABFT_BC_CLAMP ? launch_sweep_cl<true>(L, g, tm_in, tm_c, in, out, prot)
+                               : launch_sweep_cl<false>(L, g, tm_in, tm_c, in, out, prot);
 }
 
 template <class Tiles, int TY>
@@ -203,21 +210,28 @@ static cudaError_t redo_t(const Launch& L, const GridDev& g, const CUtensorMap& 
   return cudaGetLastError();
 }
 
-cudaError_t launch_redo_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                              int in, int out) {
+template <bool CL>
+static cudaError_t launch_redo_cl(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
+                                  const CUtensorMap& tm_c, int in, int out) {
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return redo_t<ShallowTiles<8>, 8>(L, g, tm_in, tm_c, in, out);
-      case 16: return redo_t<ShallowTiles<16>, 16>(L, g, tm_in, tm_c, in, out);
+      case 8: return redo_t<ShallowTiles<8, CL>, 8>(L, g, tm_in, tm_c, in, out);
+      case 16: return redo_t<ShallowTiles<16, CL>, 16>(L, g, tm_in, tm_c, in, out);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return redo_t<StreamTiles<8>, 8>(L, g, tm_in, tm_c, in, out);
-    case 16: return redo_t<StreamTiles<16>, 16>(L, g, tm_in, tm_c, in, out);
-    case 32: return redo_t<StreamTiles<32>, 32>(L, g, tm_in, tm_c, in, out);
+    case 8: return redo_t<StreamTiles<8, CL>, 8>(L, g, tm_in, tm_c, in, out);
+    case 16: return redo_t<StreamTiles<16, CL>, 16>(L, g, tm_in, tm_c, in, out);
+    case 32: return redo_t<StreamTiles<32, CL>, 32>(L, g, tm_in, tm_c, in, out);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_redo_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
+                              int in, int out) {
+  return g.bc == ABFT_BC_CLAMP ? launch_redo_cl<true>(L, g, tm_in, tm_c, in, out)
+                               : launch_redo_cl<false>(L, g, tm_in, tm_c, in, out);
 }
 
 }  // namespace abft

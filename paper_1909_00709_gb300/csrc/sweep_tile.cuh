@@ -310,9 +310,57 @@ __device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const 
   tile_sync();
 }
 
-template <int TY, bool PROT, int ACC>
+// Neighbours of a thread's four points (x = gx0 .. gx0 + 3 of row y, plane z) that
+// lie outside the grid, by the boundary rule.  On entry they hold what the staged tile
+// has there: TMA fills out-of-range cells with zeros, and at a z face the caller passes
+// the centre plane (or, for whole-column tiles, the opposite face when it is staged).
+//   clamped (Fig. 2): the centre value;
+//   empty (zero): the in-plane zero fill is already right, the z faces become zero;
+//   periodic: the opposite face, read from the input grid in global memory (through
+//   L2: it was written by other CTAs in this launch or the previous one).
+// CLAMPED: compiled for the clamped rule alone (selects only); otherwise the rule is
+// read from g.bc.
+template <bool Z_STAGED, bool CLAMPED>
+__device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __restrict__ uin, int z, int y, int gx0,
+                                               int last, const float4& c, float4& n, float4& s, float4& b, float4& t,
+                                               float& w0, float& e0, float& e1, float& e2, float& e3) {
+  if (CLAMPED || g.bc == ABFT_BC_CLAMP) {
+    if (y == 0) n = c;
+    if (y == g.ny - 1) s = c;
+    if (gx0 == 0) w0 = c.x;
+    if (last == 0) e0 = c.x;
+    if (last == 1) e1 = c.y;
+    if (last == 2) e2 = c.z;
+    if (last == 3) e3 = c.w;
+    return;
+  }
+  if (g.bc == ABFT_BC_ZERO) {
+    if (z == 0) b = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (z == g.nz - 1) t = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  if (y >= g.ny || last < 0) return;  // no grid point among the four (gx0 < nx keeps the loads in the row)
+  const size_t plane = (size_t)g.ny * g.px;
+  const float* row = uin + (size_t)z * plane + (size_t)y * g.px;
+  if (y == 0) n = __ldcg(reinterpret_cast<const float4*>(row + (size_t)(g.ny - 1) * g.px + gx0));
+  if (y == g.ny - 1) s = __ldcg(reinterpret_cast<const float4*>(row - (size_t)(g.ny - 1) * g.px + gx0));
+  if (gx0 == 0) w0 = __ldcg(row + g.nx - 1);
+  if (last <= 3) {
+    const float e = __ldcg(row);
+    if (last == 0) e0 = e;
+    if (last == 1) e1 = e;
+    if (last == 2) e2 = e;
+    if (last == 3) e3 = e;
+  }
+  if (!Z_STAGED) {
+    if (z == 0) b = __ldcg(reinterpret_cast<const float4*>(row + (size_t)(g.nz - 1) * plane + gx0));
+    if (z == g.nz - 1) t = __ldcg(reinterpret_cast<const float4*>(row - (size_t)(g.nz - 1) * plane + gx0));
+  }
+}
+
+template <int TY, bool PROT, int ACC, bool CLAMPED>
 __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
-                                               float* __restrict__ uout, int txi, int tyi,
+                                               const float* __restrict__ uin, float* __restrict__ uout, int txi, int tyi,
                                                DevCtrl* __restrict__ ctrl, const SweepSmem<TY>& sm, unsigned& seq,
                                                int pbuf) {
   using Cfg = SweepCfg<TY>;
@@ -361,21 +409,16 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       const float4 c = *reinterpret_cast<const float4*>(Uc + o);
       float4 n = *reinterpret_cast<const float4*>(Uc + o - kUW);
       float4 s = *reinterpret_cast<const float4*>(Uc + o + kUW);
-      const float4 b = *reinterpret_cast<const float4*>(Ub + o);
-      const float4 t = *reinterpret_cast<const float4*>(Ut + o);
+      float4 b = *reinterpret_cast<const float4*>(Ub + o);
+      float4 t = *reinterpret_cast<const float4*>(Ut + o);
       const float4 cs = *reinterpret_cast<const float4*>(Cs + r * kTX + 4 * lane);
       float wl = __shfl_up_sync(0xffffffffu, c.w, 1);
       float er = __shfl_down_sync(0xffffffffu, c.x, 1);
       if (lane == 0) wl = Uc[o - 1];
       if (lane == 31) er = Uc[o + 4];
-      if (y == 0) n = c;
-      if (y == g.ny - 1) s = c;
-      const float w0 = gx0 == 0 ? c.x : wl;
+      float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      if (last == 0) e0 = c.x;
-      if (last == 1) e1 = c.y;
-      if (last == 2) e2 = c.z;
-      if (last == 3) e3 = c.w;
+      boundary_cells<false, CLAMPED>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
@@ -463,15 +506,6 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
   seq = base + (unsigned)nz;
   fence_proxy_async_global();  // this thread's grid stores, before any later TMA read of them
   tile_sync();             // the ring and the reduction buffer are idle again
-}
-
-template <int TY, bool PROT, int ACC>
-__device__ __forceinline__ void sweep_tile(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
-                                           float* __restrict__ uout, int txi, int tyi, long long step,
-                                           DevCtrl* __restrict__ ctrl, const DevSched& sched,
-                                           const SweepSmem<TY>& sm, unsigned& seq, int pbuf = 0) {
-  sweep_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, seq);
-  sweep_tile_run<TY, PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, sm, seq, pbuf);
 }
 
 // flips of sweep `step` at point (z, y, x), applied to v exactly as the sweep does
@@ -629,8 +663,9 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
   tile_sync();
 }
 
-template <int TY, bool PROT, int ACC>
-__device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __restrict__ uout, int txi, int tyi,
+template <int TY, bool PROT, int ACC, bool CLAMPED>
+__device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* __restrict__ uin,
+                                                 float* __restrict__ uout, int txi, int tyi,
                                                  DevCtrl* __restrict__ ctrl, const ShallowSmem<TY>& sm,
                                                  unsigned& phase, int pbuf) {
   constexpr int NW = ShallowCfg<TY>::NW;
@@ -648,8 +683,10 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
   constexpr int PLANE = (TY + 2) * kUW;
   for (int z = warp; z < nz; z += NW) {
     const float* Uz = sm.u + z * PLANE;
-    const float* Ub = z > 0 ? Uz - PLANE : Uz;
-    const float* Ut = z + 1 < nz ? Uz + PLANE : Uz;
+    // at a z face: the centre plane, or for periodic boundaries the staged opposite face
+    const bool wrap = !CLAMPED && g.bc == ABFT_BC_PERIODIC;
+    const float* Ub = z > 0 ? Uz - PLANE : (wrap ? Uz + (nz - 1) * PLANE : Uz);
+    const float* Ut = z + 1 < nz ? Uz + PLANE : (wrap ? sm.u : Uz);
     const float* Cz = sm.c + z * TY * kTX;
     AccA<ACC> acc;
     if (PROT) acc.zero();
@@ -661,21 +698,16 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, float* __rest
       const float4 c = *reinterpret_cast<const float4*>(Uz + o);
       float4 n = *reinterpret_cast<const float4*>(Uz + o - kUW);
       float4 s = *reinterpret_cast<const float4*>(Uz + o + kUW);
-      const float4 b = *reinterpret_cast<const float4*>(Ub + o);
-      const float4 t = *reinterpret_cast<const float4*>(Ut + o);
+      float4 b = *reinterpret_cast<const float4*>(Ub + o);
+      float4 t = *reinterpret_cast<const float4*>(Ut + o);
       const float4 cs = *reinterpret_cast<const float4*>(Cz + r * kTX + 4 * lane);
       float wl = __shfl_up_sync(0xffffffffu, c.w, 1);
       float er = __shfl_down_sync(0xffffffffu, c.x, 1);
       if (lane == 0) wl = Uz[o - 1];
       if (lane == 31) er = Uz[o + 4];
-      if (y == 0) n = c;
-      if (y == g.ny - 1) s = c;
-      const float w0 = gx0 == 0 ? c.x : wl;
+      float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      if (last == 0) e0 = c.x;
-      if (last == 1) e1 = c.y;
-      if (last == 2) e2 = c.z;
-      if (last == 3) e3 = c.w;
+      boundary_cells<true, CLAMPED>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
@@ -750,7 +782,10 @@ __device__ void recompute_pa_shallow(const GridDev& g, const float* __restrict__
 // ---------------------------------------------------------------- tile policies
 // The persistent and per-launch kernels are written once against these.
 
-template <int TY>
+// CL: compiled for the clamped boundary alone (the default); false: the boundary rule
+// is read from GridDev::bc (periodic, empty).  The host picks the policy by the grid's
+// rule, so the clamped kernels carry no code for the others.
+template <int TY, bool CL = true>
 struct StreamTiles {
   static constexpr int NW = SweepCfg<TY>::NW;
   SweepSmem<TY> sm;
@@ -766,9 +801,9 @@ struct StreamTiles {
     sweep_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, seq);
   }
   template <bool PROT, int ACC>
-  __device__ __forceinline__ void run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g, float* uout, int txi,
-                      int tyi, DevCtrl* ctrl, int pbuf) {
-    sweep_tile_run<TY, PROT, ACC>(tm_u, tm_c, g, uout, txi, tyi, ctrl, sm, seq, pbuf);
+  __device__ __forceinline__ void run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
+                                      const float* uin, float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
+    sweep_tile_run<TY, PROT, ACC, CL>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, sm, seq, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
@@ -776,7 +811,7 @@ struct StreamTiles {
   }
 };
 
-template <int TY>
+template <int TY, bool CL = true>
 struct ShallowTiles {
   static constexpr int NW = ShallowCfg<TY>::NW;
   ShallowSmem<TY> sm;
@@ -792,9 +827,9 @@ struct ShallowTiles {
     shallow_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, load_c);
   }
   template <bool PROT, int ACC>
-  __device__ __forceinline__ void run(const CUtensorMap*, const CUtensorMap*, const GridDev& g, float* uout, int txi, int tyi,
-                      DevCtrl* ctrl, int pbuf) {
-    shallow_tile_run<TY, PROT, ACC>(g, uout, txi, tyi, ctrl, sm, phase, pbuf);
+  __device__ __forceinline__ void run(const CUtensorMap*, const CUtensorMap*, const GridDev& g, const float* uin,
+                                      float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
+    shallow_tile_run<TY, PROT, ACC, CL>(g, uin, uout, txi, tyi, ctrl, sm, phase, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {

@@ -58,6 +58,12 @@ def test_workspace_bytes_validates(abi):
     assert abi.abft_workspace_bytes([(0, 64, 8)], o) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(tile_y=12)) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(eps=-1.0)) == 0
+    # boundary rules 0..2 (clamped, periodic, zero); the field sits where the C struct has it
+    assert o.boundary == abi.BC_CLAMP
+    for bc in (abi.BC_PERIODIC, abi.BC_ZERO):
+        assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=bc)) > 0
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=3)) == 0
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=-1)) == 0
     big = abi.abft_workspace_bytes([(1024, 1024, 256)], o)
     assert big > 4 * 1024 * 1024 * 256 * 4
     two = abi.abft_workspace_bytes([(64, 64, 8), (100, 37, 5)], o)
