@@ -25,10 +25,10 @@
 //   per sweep in the fault-free case instead of three.
 // Barrier waits are bounded: on timeout the status word is set and the launch winds
 // down instead of hanging.
+#pragma once
+
 #include <algorithm>
 #include <cstring>
-
-#pragma once
 
 #include "check_dev.cuh"
 #include "sweep_tile.cuh"
@@ -161,7 +161,10 @@ __device__ void repair_next(const GridDev& g, const float* u_s, float* u_n, void
   __syncthreads();
 }
 
-constexpr int kOnlineThreads = kSweepThreads + 32;  // eight sweep warps and one check warp
+// Eight sweep warps and one check warp.  Two such CTAs per SM hold 18 warps, five on
+// some of the SM's four register-file quarters (16,384 registers each), which caps a
+// thread at 96 registers; a 112-register cap left one CTA per SM (measured 3.4x slower).
+constexpr int kOnlineThreads = kSweepThreads + 32;
 
 template <class Tiles, int TY, int ACC>
 __global__ void __launch_bounds__(kOnlineThreads, 2)
