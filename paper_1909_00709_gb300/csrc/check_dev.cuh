@@ -25,8 +25,9 @@ __device__ __forceinline__ double load_partial(const void* p, size_t i) {
 // FP32 pairs (hi, lo) with TwoSum (error about n u^2, below FP64 rounding of the
 // total here, and at FP32 speed: GB300's FP64 rate is a small fraction of its FP32
 // rate); the pair is widened once, hi + lo in FP64.  The FP64 variant sums in FP64.
-// Every path (one thread per entry, or the persistent kernel's check warp) evaluates exactly
-// this, so results agree bit for bit.
+// Every path (one thread per entry, or a warp per 32 entries: the per-sweep check
+// kernels and the persistent kernel's check warp) evaluates exactly this, so results
+// agree bit for bit.
 constexpr int kLanes = 8;
 
 template <int ACC>
@@ -415,8 +416,8 @@ struct InterpW {
 // combined in order), the interpolation from a^t / b^t (Theorem 1), the test of Sec.
 // 3.4, the entry appended to its plane's list if it fails.  The partial loads are
 // issued eight at a time; across a warp (32 consecutive entries) every load is
-// coalesced.  Arithmetic identical to check_entry and to the persistent kernel's
-// check warp.
+// coalesced.  Arithmetic identical to check_entry and to the boxed rounds below (the
+// persistent kernel's check warp).
 template <int ACC>
 __device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, int in, int out, int e) {
   const int na = g.nz * g.nx;
@@ -531,100 +532,138 @@ __device__ __forceinline__ int check_rounds_of(const GridDev& g) {
   return g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
 }
 
+// One round of the boxed online check: 32 consecutive entries of a[z][.] or b[z][.]
+// whose tile partials arrive as one TMA box ([n partials][32 entries]).  The steps are
+// separate steps (placement of the copy, the input loads, the lane sums and the
+// finish), run in this order by one warp in check_box_round.
+struct CheckRound {
+  bool is_a;
+  int z, c, len, n;  // plane, first entry, entries per plane, partials per entry
+};
+
+__device__ __forceinline__ CheckRound check_round_at(const GridDev& g, int round) {
+  CheckRound r;
+  const int nxb = (g.nx + kCheckBox - 1) / kCheckBox;
+  const int ra = g.nz * nxb;
+  r.is_a = round < ra;
+  if (r.is_a) {
+    r.z = round / nxb;
+    r.c = (round - r.z * nxb) * kCheckBox;
+    r.len = g.nx;
+    r.n = g.nty;
+  } else {
+    const int nyb = (g.ny + kCheckBox - 1) / kCheckBox;
+    const int q = round - ra;
+    r.z = q / nyb;
+    r.c = (q - r.z * nyb) * kCheckBox;
+    r.len = g.ny;
+    r.n = g.ntx;
+  }
+  return r;
+}
+
+// one thread: start the TMA copy of the round's partial box (buffer pbuf) into buf
+template <int ACC>
+__device__ __forceinline__ void check_round_issue(const CheckRound& r, const CUtensorMap* tm_p, int pbuf,
+                                                  unsigned char* buf, uint64_t* cbar) {
+  constexpr int per = ACC == ABFT_ACC_TWOSUM ? 2 : 1;
+  fence_proxy_async();  // earlier reads of buf come before this TMA write
+  mbar_expect_tx(cbar, kCheckBox * per * (ACC == ABFT_ACC_FP64 ? 8 : 4) * r.n);
+  tma_load_3d(buf, r.is_a ? &tm_p[pbuf] : &tm_p[2 + pbuf], r.c * per, r.z, 0, cbar);
+}
+
+// Theorem 1's inputs of the lane's entry (entry c + lane; zeros past the plane's end)
+struct CheckIn {
+  double v0, v1, v2, v3, v4, cc;
+  float ef, el;
+};
+
+__device__ __forceinline__ CheckIn check_round_inputs(const GridDev& g, const CheckRound& r, int in, int lane) {
+  CheckIn q{0, 0, 0, 0, 0, 0, 0.f, 0.f};
+  const int idx = r.c + lane, len = r.len, z = r.z;
+  if (idx >= len) return q;
+  const int im = nb_index(idx, -1, len, g.bc), ip = nb_index(idx, 1, len, g.bc);
+  const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
+  const double* V = r.is_a ? g.A[in] : g.B[in];
+  q.v0 = __ldcg(V + (size_t)z * len + idx);
+  q.v1 = ld_entry(V, z, im, len);
+  q.v2 = ld_entry(V, z, ip, len);
+  q.v3 = ld_entry(V, zm, idx, len);
+  q.v4 = ld_entry(V, zp, idx, len);
+  q.cc = (r.is_a ? g.cx : g.cy)[(size_t)z * len + idx];
+  const Coef& k = g.k;
+  if (r.is_a ? edge_needed(g.bc, k.cn, k.cs) : edge_needed(g.bc, k.cw, k.ce)) {
+    const float* u = g.u[in];
+    if (r.is_a) {
+      const size_t pl = (size_t)z * g.ny * g.px;
+      q.ef = __ldcg(u + pl + idx);
+      q.el = __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + idx);
+    } else {
+      const size_t row = ((size_t)z * g.ny + idx) * g.px;
+      q.ef = __ldcg(u + row);
+      q.el = __ldcg(u + row + g.nx - 1);
+    }
+  }
+  return q;
+}
+
+// lane sum j (partials k = j, j + 8, ... of the lane's entry, ascending) from the box
+template <int ACC>
+__device__ __forceinline__ LaneSum check_round_lane(const CheckRound& r, const unsigned char* buf, int j, int lane) {
+  using T = typename PartialType<ACC>::T;
+  const T* part = reinterpret_cast<const T*>(buf);
+  LaneSum t;
+  if (r.c + lane < r.len)
+    for (int q = j; q < r.n; q += kLanes) t.add(part[q * kCheckBox + lane]);
+  return t;
+}
+
+// the lane sums merged in order 0..7, Theorem 1, the Sec. 3.4 test; results stored
+// (checksum into A/B[out], prediction into AP/BP[0]) and a failing entry listed
+template <int ACC>
+__device__ __forceinline__ void check_round_finish(const GridDev& g, const InterpW& w, const CheckRound& r,
+                                                   const CheckIn& q, LaneSum (&t)[kLanes], int out, int lane,
+                                                   unsigned* any) {
+  const int idx = r.c + lane;
+  if (idx >= r.len) return;
+#pragma unroll
+  for (int j = 1; j < kLanes; ++j) t[0].merge<ACC>(t[j]);
+  const double s = t[0].total<ACC>();
+  const Coef& k = g.k;
+  double p;
+  const size_t e = (size_t)r.z * r.len + idx;
+  if (r.is_a) {
+    const double edge = edge_needed(g.bc, k.cn, k.cs) ? edge_of(g.bc, k.cn, k.cs, q.ef, q.el) : 0.0;
+    p = interp(q.cc, q.v0, q.v1, q.v2, q.v3, q.v4, w.a0, w.cw, w.ce, w.cb, w.ct, edge);
+    g.A[out][e] = s;
+    g.AP[0][e] = p;
+  } else {
+    const double edge = edge_needed(g.bc, k.cw, k.ce) ? edge_of(g.bc, k.cw, k.ce, q.ef, q.el) : 0.0;
+    p = interp(q.cc, q.v0, q.v1, q.v2, q.v3, q.v4, w.b0, w.cn, w.cs, w.cb, w.ct, edge);
+    g.B[out][e] = s;
+    g.BP[0][e] = p;
+  }
+  if (fails(p, s, g.eps)) append_fail(g, r.z, r.is_a ? 0 : 1, idx, any);
+  note_resid(g, p, s);
+}
+
+// one warp runs a whole round: box copy and interpolation inputs in flight together,
+// then the eight lane sums, then the finish
 template <int ACC>
 __device__ __forceinline__ void check_box_round(const GridDev& g, const InterpW& w, const CUtensorMap* tm_p, int in,
                                                 int out, int pbuf, int round, unsigned char* buf, uint64_t* cbar,
                                                 unsigned& phase, DevCtrl* ctrl, unsigned* any) {
-  using T = typename PartialType<ACC>::T;
-  constexpr int per = ACC == ABFT_ACC_TWOSUM ? 2 : 1;
   const int lane = threadIdx.x & 31;
-  const int nxb = (g.nx + kCheckBox - 1) / kCheckBox;
-  const int ra = g.nz * nxb;
-  const bool is_a = round < ra;
-  int z, c, len, n;
-  const CUtensorMap* tm;
-  if (is_a) {
-    z = round / nxb;
-    c = (round - z * nxb) * kCheckBox;
-    len = g.nx; n = g.nty;
-    tm = &tm_p[pbuf];
-  } else {
-    const int nyb = (g.ny + kCheckBox - 1) / kCheckBox;
-    const int r = round - ra;
-    z = r / nyb;
-    c = (r - z * nyb) * kCheckBox;
-    len = g.ny; n = g.ntx;
-    tm = &tm_p[2 + pbuf];
-  }
-  if (lane == 0) {
-    fence_proxy_async();  // the previous round's reads of buf come before this TMA write
-    mbar_expect_tx(cbar, kCheckBox * per * (ACC == ABFT_ACC_FP64 ? 8 : 4) * n);
-    tma_load_3d(buf, tm, c * per, z, 0, cbar);
-  }
-  const int idx = c + lane;
-  const bool live = idx < len;
-  // interpolation inputs while the box is in flight
-  const int im = nb_index(idx, -1, len, g.bc), ip = nb_index(idx, 1, len, g.bc);
-  const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
-  const double* V = is_a ? g.A[in] : g.B[in];
-  const double* CC = is_a ? g.cx : g.cy;
-  const Coef& k = g.k;
-  const bool asym = is_a ? edge_needed(g.bc, k.cn, k.cs) : edge_needed(g.bc, k.cw, k.ce);
-  double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, cc = 0;
-  float ef = 0.f, el = 0.f;
-  if (live) {
-    v0 = __ldcg(V + (size_t)z * len + idx);
-    v1 = ld_entry(V, z, im, len);
-    v2 = ld_entry(V, z, ip, len);
-    v3 = ld_entry(V, zm, idx, len);
-    v4 = ld_entry(V, zp, idx, len);
-    cc = CC[(size_t)z * len + idx];
-    if (asym) {
-      const float* u = g.u[in];
-      if (is_a) {
-        const size_t pl = (size_t)z * g.ny * g.px;
-        ef = __ldcg(u + pl + idx);
-        el = __ldcg(u + pl + (size_t)(g.ny - 1) * g.px + idx);
-      } else {
-        const size_t row = ((size_t)z * g.ny + idx) * g.px;
-        ef = __ldcg(u + row);
-        el = __ldcg(u + row + g.nx - 1);
-      }
-    }
-  }
+  const CheckRound r = check_round_at(g, round);
+  if (lane == 0) check_round_issue<ACC>(r, tm_p, pbuf, buf, cbar);
+  const CheckIn q = check_round_inputs(g, r, in, lane);
   mbar_wait(cbar, phase, ctrl);
   phase ^= 1u;
-  const T* part = reinterpret_cast<const T*>(buf);
   LaneSum t[kLanes];
-  if (live) {
-    int q = 0;
-    for (; q + kLanes <= n; q += kLanes) {
 #pragma unroll
-      for (int j = 0; j < kLanes; ++j) t[j].add(part[(q + j) * kCheckBox + lane]);
-    }
-#pragma unroll
-    for (int j = 0; j < kLanes; ++j)
-      if (q + j < n) t[j].add(part[(q + j) * kCheckBox + lane]);
-  }
-  __syncwarp();
-  if (!live) return;
-#pragma unroll
-  for (int j = 1; j < kLanes; ++j) t[0].merge<ACC>(t[j]);
-  const double s = t[0].total<ACC>();
-  double p;
-  if (is_a) {
-    const double edge = asym ? edge_of(g.bc, k.cn, k.cs, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, w.a0, w.cw, w.ce, w.cb, w.ct, edge);
-    g.A[out][(size_t)z * len + idx] = s;
-    g.AP[0][(size_t)z * len + idx] = p;
-  } else {
-    const double edge = asym ? edge_of(g.bc, k.cw, k.ce, ef, el) : 0.0;
-    p = interp(cc, v0, v1, v2, v3, v4, w.b0, w.cn, w.cs, w.cb, w.ct, edge);
-    g.B[out][(size_t)z * len + idx] = s;
-    g.BP[0][(size_t)z * len + idx] = p;
-  }
-  if (fails(p, s, g.eps)) append_fail(g, z, is_a ? 0 : 1, idx, any);
-  note_resid(g, p, s);
+  for (int j = 0; j < kLanes; ++j) t[j] = check_round_lane<ACC>(r, buf, j, lane);
+  __syncwarp();  // every lane has read buf before lane 0 may start the next copy into it
+  check_round_finish<ACC>(g, w, r, q, t, out, lane, any);
 }
 
 }  // namespace abft
