@@ -607,15 +607,24 @@ __device__ __forceinline__ CheckIn check_round_inputs(const GridDev& g, const Ch
   return q;
 }
 
-// lane sum j (partials k = j, j + 8, ... of the lane's entry, ascending) from the box
+// the eight lane sums of the lane's entry from the box: lane sum j takes partials
+// k = j, j + 8, ... in ascending order; the eight are advanced together (eight
+// independent shared-memory loads per step), which keeps one warp's round short
 template <int ACC>
-__device__ __forceinline__ LaneSum check_round_lane(const CheckRound& r, const unsigned char* buf, int j, int lane) {
+__device__ __forceinline__ void check_round_lanes(const CheckRound& r, const unsigned char* buf, int lane,
+                                                  LaneSum (&t)[kLanes]) {
   using T = typename PartialType<ACC>::T;
   const T* part = reinterpret_cast<const T*>(buf);
-  LaneSum t;
-  if (r.c + lane < r.len)
-    for (int q = j; q < r.n; q += kLanes) t.add(part[q * kCheckBox + lane]);
-  return t;
+  if (r.c + lane >= r.len) return;
+  const int n = r.n;
+  int q = 0;
+  for (; q + kLanes <= n; q += kLanes) {
+#pragma unroll
+    for (int j = 0; j < kLanes; ++j) t[j].add(part[(q + j) * kCheckBox + lane]);
+  }
+#pragma unroll
+  for (int j = 0; j < kLanes; ++j)
+    if (q + j < n) t[j].add(part[(q + j) * kCheckBox + lane]);
 }
 
 // the lane sums merged in order 0..7, Theorem 1, the Sec. 3.4 test; results stored
@@ -660,8 +669,7 @@ __device__ __forceinline__ void check_box_round(const GridDev& g, const InterpW&
   mbar_wait(cbar, phase, ctrl);
   phase ^= 1u;
   LaneSum t[kLanes];
-#pragma unroll
-  for (int j = 0; j < kLanes; ++j) t[j] = check_round_lane<ACC>(r, buf, j, lane);
+  check_round_lanes<ACC>(r, buf, lane, t);
   __syncwarp();  // every lane has read buf before lane 0 may start the next copy into it
   check_round_finish<ACC>(g, w, r, q, t, out, lane, any);
 }
