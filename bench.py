@@ -370,6 +370,18 @@ def side_runs(dev, stream, flush):
                 r[mname], _ = timed(shape, mode, sweeps, 6, boundary=bcv)
             r["overhead_pct"] = {k: (r["unprotected"] / v - 1.0) * 100.0 for k, v in r.items() if k != "unprotected"}
             bnd.setdefault(bname, {})["x".join(map(str, shape))] = r
+    # one checksum vector per sweep (Sec. 3.2: b tested every sweep, a summed only where b
+    # failed), against the default of both vectors, on the benchmark grid and the large one
+    onev = {}
+    for shape, sweeps, rate in ((SHAPE, SWEEPS, RATE), (LARGE_SHAPE, LARGE_SWEEPS, 1.0)):
+        r = {"unprotected": timed(shape, abi.MODE_NONE, sweeps, 4)[0]}
+        for vec in (2, 1):
+            r[f"online_{vec}_vectors"] = timed(shape, abi.MODE_ONLINE, sweeps, 4, vectors=vec)[0]
+            r[f"online_{vec}_vectors_flips"] = timed(shape, abi.MODE_ONLINE, sweeps, 4, inject=rate, vectors=vec,
+                                                     max_flips_per_step=64)[0]
+        r["overhead_pct"] = {k: (r["unprotected"] / v - 1.0) * 100.0 for k, v in r.items() if k != "unprotected"}
+        r["flips_per_sweep"] = rate
+        onev["x".join(map(str, shape))] = r
     large = {}
     lam = 1e-6 * math.prod(LARGE_SHAPE)  # flips per sweep
     for name, mode, rate in (("unprotected", abi.MODE_NONE, 0.0), ("online", abi.MODE_ONLINE, 0.0),
@@ -470,7 +482,8 @@ def side_runs(dev, stream, flush):
         errs = np.array(errs)
         errcamp[name] = {"median_l2": float(np.median(errs)), "mean_l2": float(np.mean(errs[np.isfinite(errs)])),
                          "share_exact": float(np.mean(errs == 0.0))}
-    return {"boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16}, "batch": batch,
+    return {"boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16},
+            "one_vector": {"glups": onev, "mode": "online; *_flips at the stated rate"}, "batch": batch,
             "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
             "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
                           "variants": prec},

@@ -122,6 +122,12 @@ typedef struct {
                                of graph_steps sweeps); 0: grid by grid. Offline steps always go
                                grid by grid. */
   int32_t boundary;         /* abft_boundary of every grid of the context */
+  int32_t vectors;          /* online checks: 2 = test both checksum vectors every sweep; 1 = test
+                               b (sums along x) every sweep and compute a, from the grid, only in
+                               planes where b failed, to locate (Sec. 3.2: one vector detects, the
+                               second is needed only after a detection).  1 finds the same faults
+                               where b's threshold is not above a's (nx <= ny) and skips the a
+                               partials and a checks; offline and unprotected steps ignore it */
   void* stream;             /* cudaStream_t used for all device work */
 } abft_options;
 
@@ -149,7 +155,7 @@ typedef struct {
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
    sweeps, default tile, 64 flips per step, persistent launches, whole-column tiles for
    shallow grids, no residual tracking, depth 1, overlapped checks, batched launches,
-   clamped boundaries, NULL stream. */
+   clamped boundaries, both checksum vectors, NULL stream. */
 ABFT_API void abft_default_options(abft_options* opt);
 
 /* Bytes of device workspace abft_init needs for these grids and options

@@ -46,7 +46,7 @@ class _Stencil(ct.Structure):
 
 class _Opts(ct.Structure):
     _fields_ = [("eps", ct.c_double), ("delta", ct.c_int32), ("literal_eq8", ct.c_int32),
-                ("band_lo", ct.c_double), ("band_hi", ct.c_double)]
+                ("band_lo", ct.c_double), ("band_hi", ct.c_double), ("vectors", ct.c_int32)]
 
 
 class _Out(ct.Structure):
@@ -187,8 +187,9 @@ def _as_flips(flips) -> np.ndarray:
 
 def run(st: Stencil, C, u0, nsteps: int, mode: int, flips=None, *, t0: int = 0,
         eps: float = 1e-5, delta: int = 16, literal_eq8: bool = False,
-        band=(0.95, 1.05), ev_cap: int = 1 << 16, marg_cap: int = 1 << 16) -> dict:
-    """Run `nsteps` sweeps from u0 (FP64 copy) in the given mode.
+        band=(0.95, 1.05), vectors: int = 2, ev_cap: int = 1 << 16, marg_cap: int = 1 << 16) -> dict:
+    """Run `nsteps` sweeps from u0 (FP64 copy) in the given mode (`vectors`: 2 tests both
+    checksum vectors every sweep, 1 tests b and consults a only where b failed).
 
     Returns the final grid, the event list, the (step, plane) pairs whose residual
     fell inside the guard band, the largest relative residual, rollbacks and flips."""
@@ -198,7 +199,7 @@ def run(st: Stencil, C, u0, nsteps: int, mode: int, flips=None, *, t0: int = 0,
     ev = np.zeros(ev_cap, dtype=EVENT)
     ms = np.zeros(marg_cap, dtype=np.int64)
     mz = np.zeros(marg_cap, dtype=np.int32)
-    o = _Opts(eps, delta, int(literal_eq8), band[0], band[1])
+    o = _Opts(eps, delta, int(literal_eq8), band[0], band[1], int(vectors))
     r = _Out(ev.ctypes.data, ev_cap, 0, ms.ctypes.data, mz.ctypes.data, marg_cap, 0, 0.0, 0, 0)
     rc = _load().orc_run(ct.byref(st.c), _ptr(C), _ptr(u), t0, nsteps, mode,
                          _ptr(fl) if len(fl) else None, len(fl), ct.byref(o), ct.byref(r))

@@ -411,8 +411,10 @@ int orc_run(const orc_stencil* s, const double* C, double* u, int64_t t0, int64_
       inject(s, flips, nflips, t, ORC_TARGET_B, uq, An, Bn, r);
       orc_interpolate(s, cx, cy, A, B, u, Ap, Bp);                  /* Theorem 1     */
       for (int32_t z = 0; z < nz; z++) {                            /* Theorem 2     */
-        const int64_t nfa = compare_line(o, r, t, z, nx, Ap + z * nx, An + z * nx, fa);
         const int64_t nfb = compare_line(o, r, t, z, ny, Bp + z * ny, Bn + z * ny, fb);
+        /* one-vector detection (Sec. 3.2): a is consulted only after b detected */
+        const int64_t nfa = (o->vectors == 1 && nfb == 0)
+                                ? 0 : compare_line(o, r, t, z, nx, Ap + z * nx, An + z * nx, fa);
         if (nfa == 1 && nfb == 1)
           correct_point(s, o, r, t, z, fa[0], fb[0], uq, An, Bn, Ap, Bp); /* Eq. (8) */
         else if (nfa + nfb > 0)

@@ -43,6 +43,9 @@ typedef struct {
   int32_t delta;       /* offline detection period (Sec. 4.1) */
   int32_t literal_eq8; /* 1: evaluate Eq. (8) as a' - (a - u); 0: as a' - sum of the others */
   double band_lo, band_hi; /* guard band on |a'-a| / (eps |a|) that is logged as marginal */
+  int32_t vectors;     /* online: 2 = test a and b every sweep; 1 = test b every sweep and a only
+                          in planes where b failed (Sec. 3.2: one vector detects, the second
+                          locates and is needed only after a detection) */
 } orc_opts;
 
 typedef struct {

@@ -44,7 +44,7 @@ class abft_options(ct.Structure):
                 ("event_capacity", ct.c_int32), ("graph_steps", ct.c_int32), ("tile_y", ct.c_int32),
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
                 ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("overlap", ct.c_int32),
-                ("batch", ct.c_int32), ("boundary", ct.c_int32),
+                ("batch", ct.c_int32), ("boundary", ct.c_int32), ("vectors", ct.c_int32),
                 ("stream", ct.c_void_p)]
 
 

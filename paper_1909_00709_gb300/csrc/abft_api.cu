@@ -37,11 +37,12 @@ struct GridPlan {
   size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx, tdirty;
 };
 
-// per-launch control words of a grid: fails[3], redo, bar, bars[3] (zeroed before every
-// persistent launch)
+// per-launch control words of a grid: fails[3], redo, nbz, bar, bars[3] (zeroed before
+// every persistent launch)
 constexpr size_t kLaunchCtrlBytes = offsetof(DevGridCtrl, verdict) - offsetof(DevGridCtrl, fails);
 static_assert(offsetof(DevGridCtrl, redo) == offsetof(DevGridCtrl, fails) + 3 * sizeof(unsigned) &&
-                  offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, redo) + sizeof(unsigned) &&
+                  offsetof(DevGridCtrl, nbz) == offsetof(DevGridCtrl, redo) + sizeof(unsigned) &&
+                  offsetof(DevGridCtrl, bar) == offsetof(DevGridCtrl, nbz) + 2 * sizeof(unsigned) &&
                   offsetof(DevGridCtrl, bars) == offsetof(DevGridCtrl, bar) + sizeof(unsigned long long) &&
                   offsetof(DevGridCtrl, verdict) == offsetof(DevGridCtrl, bars) + 3 * sizeof(unsigned long long),
               "per-launch control words must be contiguous");
@@ -75,7 +76,7 @@ bool valid_options(const abft_options& o) {
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
          (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1) &&
          o.depth >= 1 && o.depth <= 4 && (o.overlap == 0 || o.overlap == 1) && o.boundary >= ABFT_BC_CLAMP &&
-         o.boundary <= ABFT_BC_ZERO;
+         o.boundary <= ABFT_BC_ZERO && (o.vectors == 1 || o.vectors == 2);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -278,7 +279,8 @@ struct abft_ctx {
   std::vector<CUtensorMap> tm_tb;  // temporal blocking (depth >= 2): u[0..2], C per grid
   std::vector<int> cur, ref;
   std::vector<int64_t> ref_step;
-  std::vector<char> ck_valid;
+  std::vector<char> ck_valid;  // A/B[cur] are the current state's checksums: 0 no, 1 both, 2 only B
+  std::vector<char> ref_ck;    // the same for A/B[ref], the verified state
   int64_t step = 0;
   DevCtrl* ctrl = nullptr;
   DevGridCtrl* gctrl = nullptr;
@@ -464,14 +466,19 @@ abft_status read_ctrl(abft_ctx* ctx) {
   return ABFT_OK;
 }
 
-// make A[cur], B[cur] the checksums of the current state (trusted, Theorem 2's premise)
-abft_status ensure_checksums(abft_ctx* ctx, int gi) {
-  if (ctx->ck_valid[gi]) return ABFT_OK;
+// what an online sweep leaves valid: both vectors, or only B with one-vector checks
+char online_ck(const GridDev& g) { return g.vec == 1 ? 2 : 1; }
+
+// make A[cur], B[cur] the checksums of the current state (trusted, Theorem 2's premise);
+// need_a = false: B alone suffices (one-vector online checks)
+abft_status ensure_checksums(abft_ctx* ctx, int gi, bool need_a = true) {
+  if (ctx->ck_valid[gi] == 1 || (!need_a && ctx->ck_valid[gi] == 2)) return ABFT_OK;
   const GridDev& g = ctx->g[gi];
   const int c = ctx->cur[gi];
   const Launch L = launcher(ctx);
   CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.A[c], g.B[c]); }));
   ctx->ck_valid[gi] = 1;
+  if (ctx->ref[gi] == c) ctx->ref_ck[gi] = 1;
   return ABFT_OK;
 }
 
@@ -481,7 +488,7 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
   const bool prot = mode == ABFT_MODE_ONLINE;
   for (int gi = 0; gi < ctx->n; ++gi) {
     if (prot) {
-      abft_status s = ensure_checksums(ctx, gi);
+      abft_status s = ensure_checksums(ctx, gi, ctx->g[gi].vec != 1);
       if (s) return s;
     }
     const GridDev& g = ctx->g[gi];
@@ -508,7 +515,7 @@ abft_status persistent_all(abft_ctx* ctx, int64_t n, int mode) {
     if (prot) {
       ctx->ref[gi] = ctx->cur[gi];
       ctx->ref_step[gi] = ctx->step + n;
-      ctx->ck_valid[gi] = 1;
+      ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(g);
     } else {
       ctx->ck_valid[gi] = 0;
     }
@@ -541,7 +548,7 @@ abft_status persistent_offline_all(abft_ctx* ctx, int64_t n) {
     ctx->cur[gi] = c;
     ctx->ref[gi] = c;
     ctx->ref_step[gi] = ctx->step + n;
-    ctx->ck_valid[gi] = 1;
+    ctx->ck_valid[gi] = ctx->ref_ck[gi] = 1;
   }
   ctx->step += n;
   return ABFT_OK;
@@ -562,7 +569,7 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
       ctx->cur[gi] = out;
       ctx->ref[gi] = out;
       ctx->ref_step[gi] = ctx->step + 1;
-      ctx->ck_valid[gi] = 1;
+      ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(g);
     } else {
       const int out = other_than(in, ctx->ref[gi]);
       CK(run(ctx, kKSweepPlain, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, false); }));
@@ -620,7 +627,7 @@ abft_status online_overlap(abft_ctx* ctx, int64_t n) {
     ctx->cur[gi] = out;
     ctx->ref[gi] = out;
     ctx->ref_step[gi] = s + 1;
-    ctx->ck_valid[gi] = 1;
+    ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(g);
     ++ctx->step;
   }
   CK(cudaStreamWaitEvent(A.s, ctx->join_ev, 0));  // the last check and its fixes
@@ -692,8 +699,8 @@ void build_batch_tables(abft_ctx* ctx) {
   for (int i = 0; i < n; ++i) {
     const GridDev& g = ctx->g[i];
     grids.push_back(i);
-    const int64_t rounds = box ? (int64_t)g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox)
-                               : ((int64_t)g.nz * (g.nx + g.ny) + 31) / 32;
+    const int64_t rounds = box ? check_rounds_host(g)
+                               : ((int64_t)g.nz * (g.nx + g.ny) - check_entries_first(g) + 31) / 32;
     koff.push_back(koff.back() + (int)((rounds + per_block - 1) / per_block));
   }
   k.n = n;
@@ -790,7 +797,7 @@ abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
   const bool prot = mode == ABFT_MODE_ONLINE;
   if (prot)
     for (int gi = 0; gi < ctx->n; ++gi) {
-      abft_status s = ensure_checksums(ctx, gi);
+      abft_status s = ensure_checksums(ctx, gi, ctx->g[gi].vec != 1);
       if (s) return s;
     }
   for (const auto& b : ctx->bcls) CK(batch_prepare(b.shallow, b.ty, prot, ctx->opt.acc, ctx->opt.boundary, b.smem));
@@ -827,7 +834,7 @@ abft_status batch_all(abft_ctx* ctx, int64_t n, int mode) {
       ctx->cur[gi] = (int)((r.first + n) % 3);
       ctx->ref[gi] = ctx->cur[gi];
       ctx->ref_step[gi] = ctx->step + n;
-      ctx->ck_valid[gi] = 1;
+      ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(ctx->g[gi]);
     } else {
       ctx->cur[gi] = ((n - 1) & 1) ? r.b : r.a;
       ctx->ck_valid[gi] = 0;
@@ -1004,7 +1011,7 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   for (int gi = 0; gi < ctx->n; ++gi) {
     ctx->ref[gi] = ctx->cur[gi];
     ctx->ref_step[gi] = ctx->step;
-    ctx->ck_valid[gi] = 1;
+    ctx->ck_valid[gi] = ctx->ref_ck[gi] = 1;
   }
   return ABFT_OK;
 }
@@ -1031,6 +1038,7 @@ void abft_default_options(abft_options* o) {
   o->persistent = 1;
   o->shallow = 1;
   o->boundary = ABFT_BC_CLAMP;
+  o->vectors = 2;
   o->stream = nullptr;
 }
 
@@ -1164,6 +1172,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.acc = opt->acc;
     g.gid = i;
     g.bc = opt->boundary;
+    g.vec = opt->vectors;
     g.eps = opt->eps;
     const abft_coeffs& c = coeffs[i];
     g.k = Coef{c.cc, c.cw, c.ce, c.cn, c.cs, c.cb, c.ct};
@@ -1194,6 +1203,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   ctx->ref.assign(n_grids, 0);
   ctx->ref_step.assign(n_grids, 0);
   ctx->ck_valid.assign(n_grids, 1);
+  ctx->ref_ck.assign(n_grids, 1);
   cudaStream_t s = ctx->stream;
 #define CKI(call)                                                                              \
   do {                                                                                         \
@@ -1328,7 +1338,7 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
       }
       if (mode == ABFT_MODE_ONLINE)
         for (int gi = 0; gi < ctx->n; ++gi) {
-          s = ensure_checksums(ctx, gi);
+          s = ensure_checksums(ctx, gi, ctx->g[gi].vec != 1);
           if (s) return s;
         }
       if (mode == ABFT_MODE_ONLINE && ctx->n == 1 && ctx->opt.overlap && !ctx->timing) {
@@ -1358,6 +1368,11 @@ abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
     ctx->v_dist[gi] = d;
     if (d > 0 && !offline_capable(ctx->co[gi], ctx->opt.boundary))
       return fail(ctx, ABFT_E_INVAL, "chained verification needs vanishing boundary terms (grid %d)", gi);
+    if (ctx->ref_ck[gi] != 1) {  // one-vector checks left a of the verified state unsummed
+      CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[r], g.A[r], g.B[r]); }));
+      ctx->ref_ck[gi] = 1;
+      if (r == c) ctx->ck_valid[gi] = 1;
+    }
     CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.AP[2], g.BP[2]); }));
     const double* pa = g.A[r];
     const double* pb = g.B[r];

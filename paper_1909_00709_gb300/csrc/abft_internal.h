@@ -58,12 +58,16 @@ struct DevGridCtrl {
   unsigned int rollbacks;   // offline windows the persistent kernel recomputed
   unsigned int fails[3];    // failing entries found by the persistent kernel, by sweep index mod 3
   unsigned int redo;         // 1: a correction was made after the next sweep had started (per-launch overlap)
+  unsigned int nbz;          // one-vector checks: planes whose b failed this sweep (list bz)
+  unsigned int pad;          // keeps bar 8-byte aligned right after
   unsigned long long bar;   // grid barrier of the persistent kernel: arrivals since launch
   unsigned long long bars[3];  // payload barrier (online kernel): per instance mod 3, arrivals | payload << 32
   unsigned long long verdict;  // failing entries of the last offline/verify comparison
   unsigned long long unresolved;  // planes a zero-distance correction could not fix
   unsigned long long max_resid;   // bits of the largest |a'-a|/|a| of a passing entry (when tracked)
+  int bz[64];                     // the first of those planes (kBzCap)
 };
+constexpr int kBzCap = 64;
 
 // everything a kernel needs to know about one grid (passed by value)
 struct GridDev {
@@ -76,6 +80,7 @@ struct GridDev {
   int track;                // 1: keep the running maximum of the passing residuals
   int gid;
   int bc;                   // abft_boundary: what a neighbour outside the grid reads
+  int vec;                  // checksum vectors the online check tests every sweep (2: a and b; 1: b)
   Coef k;
   double eps;
   float* u[3];              // state buffers
@@ -143,6 +148,12 @@ cudaError_t launch_check_online(const Launch& L, const GridDev& g, const Partial
 // the box check needs at most 256 tiles along x and along y
 bool check_box_usable(const GridDev& g);
 int check_box_bytes_host(int nty, int ntx, int acc);
+// 32-entry rounds of one online check (only the b entries with one vector)
+inline long long check_rounds_host(const GridDev& g) {
+  return (long long)g.nz * ((g.vec == 1 ? 0 : (g.nx + kCheckBox - 1) / kCheckBox) + (g.ny + kCheckBox - 1) / kCheckBox);
+}
+// entries [first, nz (nx + ny)) of one online check: a[z][x] first, then b[z][y]
+inline long long check_entries_first(const GridDev& g) { return g.vec == 1 ? (long long)g.nz * g.nx : 0; }
 int check_box_warps(int box_bytes);
 // location and correction after launch_check_online, one block per plane
 // `step`: the sweep whose output is checked (event stamps); a resolved plane sets the

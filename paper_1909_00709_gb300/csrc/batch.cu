@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256)
     for (int r = lb * nw + warp; r < rounds; r += nb * nw)
       check_box_round<ACC>(g, iw, tm_p, 0, 1, 0, r, buf, bar, phase, ctrl, nullptr);
   } else {
-    check_warps<ACC>(g, 0, 1, lb * nw + warp, nb * nw, g.nz * (g.nx + g.ny));
+    check_warps<ACC>(g, 0, 1, lb * nw + warp, nb * nw, g.vec == 1 ? g.nz * g.nx : 0, g.nz * (g.nx + g.ny));
   }
   __shared__ int s_last;
   __threadfence();

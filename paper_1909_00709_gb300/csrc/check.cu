@@ -21,9 +21,9 @@ __global__ void __launch_bounds__(kCheckThreads)
     k_check_online(const GridDev g, int in, int out, DevCtrl* ctrl, abft_event* ev) {
   (void)ctrl;
   (void)ev;
-  const int n = g.nz * (g.nx + g.ny);
+  const int n = g.nz * (g.nx + g.ny), first = g.vec == 1 ? g.nz * g.nx : 0;
   const int nw = kCheckThreads / 32;
-  check_warps<ACC>(g, in, out, blockIdx.x * nw + (int)(threadIdx.x >> 5), gridDim.x * nw, n);
+  check_warps<ACC>(g, in, out, blockIdx.x * nw + (int)(threadIdx.x >> 5), gridDim.x * nw, first, n);
 }
 
 // The same check with the partials brought in by TMA: warp w of a block takes rounds
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kCheckThreads)
     __syncthreads();  // every thread has read s_hit before thread 0 rewrites it
     if (hit) {
       resolve_plane(sm, g, g.u[in], g.u[out], g.A[out], g.B[out], g.AP[0], g.BP[0], step, ctrl, ev,
-                    &g.gc->unresolved, z);
+                    &g.gc->unresolved, z, g.vec == 1);
       // u[out] changed: a next sweep already started is stale in every tile whose
       // stencil read a changed point (with periodic boundaries a fix on a face also
       // reaches the opposite face: every tile row or column, or every plane)
@@ -96,6 +96,15 @@ __global__ void __launch_bounds__(kCheckThreads)
       __syncthreads();
     }
   }
+  // the plane list of the one-vector check was consumed by k_demand_sums (an earlier
+  // launch); the next check starts a new one
+  if (g.vec == 1 && blockIdx.x == 0 && threadIdx.x == 0) g.gc->nbz = 0;
+}
+
+// One-vector checks (Sec. 3.2): the on-demand column sums before the location step, as
+// a launch of its own (per-launch paths; the persistent kernel runs demand_sums itself).
+__global__ void __launch_bounds__(256) k_demand_sums(const GridDev g, int in, int out) {
+  demand_sums(g, g.u[in], g.u[out], g.A[out], g.AP[1], blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ offline pieces
@@ -241,7 +250,7 @@ cudaError_t launch_check_online(const Launch& L, const GridDev& g, const Partial
     const int box = (check_box_bytes(g.nty, g.ntx, g.acc) + 127) / 128 * 128;
     const int nw = std::min(check_box_warps(box), std::max(max_warps, 1));
     const int smem = 256 + nw * box;
-    const long long rounds = (long long)g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
+    const long long rounds = check_rounds_host(g);
     const int blocks = (int)std::min<long long>((rounds + nw - 1) / nw, (nw == 1 ? 8LL : 4LL) * sm_count());
     cudaError_t e = cudaSuccess;
     switch (g.acc) {
@@ -262,8 +271,8 @@ cudaError_t launch_check_online(const Launch& L, const GridDev& g, const Partial
     return cudaGetLastError();
   }
   // 32 entries per warp, up to one wave of 8 blocks per SM; further entries by striding
-  const int blocks =
-      (int)std::min<long long>(((long long)g.nz * (g.nx + g.ny) + kCheckThreads - 1) / kCheckThreads, 8LL * sm_count());
+  const long long entries = (long long)g.nz * (g.nx + g.ny) - check_entries_first(g);
+  const int blocks = (int)std::min<long long>((entries + kCheckThreads - 1) / kCheckThreads, 8LL * sm_count());
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: k_check_online<ABFT_ACC_TWOSUM><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
     case ABFT_ACC_FP64: k_check_online<ABFT_ACC_FP64><<<blocks, kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events); break;
@@ -273,6 +282,11 @@ cudaError_t launch_check_online(const Launch& L, const GridDev& g, const Partial
 }
 
 cudaError_t launch_resolve(const Launch& L, const GridDev& g, int in, int out, long long step) {
+  if (g.vec == 1) {
+    k_demand_sums<<<2 * sm_count(), 256, 0, L.s>>>(g, in, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_resolve<<<std::min(g.nz, 1024), kCheckThreads, 0, L.s>>>(g, in, out, L.ctrl, L.events, step);
   return cudaGetLastError();
 }

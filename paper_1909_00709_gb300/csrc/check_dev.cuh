@@ -188,6 +188,10 @@ __device__ __forceinline__ void append_fail(const GridDev& g, int z, int which, 
   const int k = atomicAdd(&g.fcnt[2 * z + which], 1);
   if (k < kFCap) g.fidx[(size_t)(2 * z + which) * kFCap + k] = idx;
   if (any) atomicAdd(any, 1u);
+  if (g.vec == 1 && which == 1 && k == 0) {  // one-vector checks: list the plane once
+    const unsigned j = atomicAdd(&g.gc->nbz, 1u);
+    if (j < (unsigned)kBzCap) g.gc->bz[j] = z;
+  }
 }
 
 // ------------------------------------------------ plane resolution (one block)
@@ -322,9 +326,115 @@ static __device__ void sort_small(int* v, int n) {
 // previous state is available: only single intersections can then be corrected,
 // other patterns are counted in *unresolved.  Planes are independent, so blocks may
 // resolve different planes at the same time.
+// One-vector checks (Sec. 3.2): plane z's b entries failed, its a entries were not
+// tested.  a^t of the planes Theorem 1 reads (z and its z neighbours under the boundary
+// rule) is summed from the previous state uin into the scratch vector at, a^{t+1}[z]
+// from u into A, the interpolation of a^{t+1}[z] goes to ap, and the failing a entries
+// are listed -- what the two-vector check would have found.  Column sums in the order
+// recompute_lines uses (compensated FP32, eight interleaved row lanes).
+static __device__ void column_sums(const GridDev& g, const float* u, int z, double* out) {
+  const size_t pl = (size_t)z * g.ny * g.px;
+  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+    LaneSum L[8];
+    int y = 0;
+    for (; y + 8 <= g.ny; y += 8)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) L[j].add(__ldcg(u + pl + (size_t)(y + j) * g.px + x));
+    for (int j = 0; y + j < g.ny; ++j) L[j].add(__ldcg(u + pl + (size_t)(y + j) * g.px + x));
+#pragma unroll
+    for (int j = 1; j < 8; ++j) L[0].merge<ABFT_ACC_TWOSUM>(L[j]);
+    out[(size_t)z * g.nx + x] = L[0].total<ABFT_ACC_TWOSUM>();
+  }
+}
+
+// For every plane z whose b entries failed (listed by the check), the column sums
+// a^{t+1}[z] of uout (into Aout) and a^t of the planes Theorem 1 reads, z and its z
+// neighbours, of uin (into the scratch at).  Work item (plane, k, 32 columns), items
+// b0, b0 + stride, ... for this block: eight warps of 32 threads, thread (j, column) sums
+// the rows y = j mod 8 (compensated FP32), merged in order -- the arithmetic of
+// column_sums, spread over many blocks so that large planes are summed at bandwidth.
+// With no failure the block leaves after one load; past the list's capacity every plane
+// is visited and its failure count consulted.  Threads beyond the first 256 only join
+// the block barriers.
+static __device__ void demand_sums(const GridDev& g, const float* uin, const float* uout, double* Aout, double* at,
+                                   int b0, int stride) {
+  __shared__ __align__(16) unsigned char raw[8 * 32 * sizeof(LaneSum)];
+  LaneSum(*L)[32] = reinterpret_cast<LaneSum(*)[32]>(raw);
+  const unsigned nb = __ldcg(&g.gc->nbz);
+  if (nb == 0) return;
+  const bool listed = nb <= (unsigned)kBzCap;
+  const int nxb = (g.nx + 31) / 32;
+  const long long items = (long long)(listed ? (int)nb : g.nz) * 4 * nxb;
+  const int col = threadIdx.x & 31, j = threadIdx.x >> 5;
+  for (long long it = b0; it < items; it += stride) {
+    const int p = (int)(it / (4 * nxb)), rem = (int)(it % (4 * nxb));
+    const int k = rem / nxb, xb = rem % nxb;
+    const int z = listed ? __ldcg(&g.gc->bz[p]) : p;
+    if (!listed && __ldcg(&g.fcnt[2 * z + 1]) == 0) continue;  // uniform over the block
+    const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
+    int pz = z;
+    if (k == 1) {
+      if (zm < 0 || zm == z) continue;
+      pz = zm;
+    } else if (k == 3) {
+      if (zp < 0 || zp == z || zp == zm) continue;
+      pz = zp;
+    }
+    const float* u = k == 0 ? uout : uin;
+    double* dst = k == 0 ? Aout : at;
+    const int x = xb * 32 + col;
+    if (j < 8) {
+      LaneSum t;
+      if (x < g.nx) {
+        const float* q = u + (size_t)pz * g.ny * g.px + x;
+        for (int y = j; y < g.ny; y += 8) t.add(__ldcg(q + (size_t)y * g.px));
+      }
+      L[j][col] = t;
+    }
+    __syncthreads();
+    if (j == 0 && x < g.nx) {
+      LaneSum s = L[0][col];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) s.merge<ABFT_ACC_TWOSUM>(L[q][col]);
+      dst[(size_t)pz * g.nx + x] = s.total<ABFT_ACC_TWOSUM>();
+    }
+    __syncthreads();  // L is reused by the next item
+  }
+}
+
+static __device__ void demand_a(const GridDev& g, const float* uin, const float* u, double* A, double* ap,
+                                double* at, int z, bool summed) {
+  if (!summed) {  // otherwise k_demand_sums formed them, in the same order
+    const int zm = nb_index(z, -1, g.nz, g.bc), zp = nb_index(z, 1, g.nz, g.bc);
+    column_sums(g, uin, z, at);
+    if (zm >= 0 && zm != z) column_sums(g, uin, zm, at);
+    if (zp >= 0 && zp != z && zp != zm) column_sums(g, uin, zp, at);
+    column_sums(g, u, z, A);
+    __threadfence_block();
+    __syncthreads();
+  }
+  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+    const double p = predict_a(g, at, uin, z, x);
+    const double s = A[(size_t)z * g.nx + x];
+    ap[(size_t)z * g.nx + x] = p;
+    if (fails(p, s, g.eps)) append_fail(g, z, 0, x);
+    note_resid(g, p, s);
+  }
+  __threadfence_block();
+  __syncthreads();
+}
+
 static __device__ void resolve_plane(ResolveSmem& sm, const GridDev& g, const float* uin, float* u, double* A,
                                      double* B, const double* ap, const double* bp, long long step, DevCtrl* ctrl,
-                                     abft_event* ev, unsigned long long* unresolved, int z) {
+                                     abft_event* ev, unsigned long long* unresolved, int z, bool a_summed = false) {
+  if (g.vec == 1 && uin != nullptr) {
+    __shared__ int s_nb;
+    if (threadIdx.x == 0) s_nb = __ldcg(&g.fcnt[2 * z + 1]);
+    __syncthreads();
+    const bool b_failed = s_nb != 0;
+    __syncthreads();
+    if (b_failed) demand_a(g, uin, u, A, const_cast<double*>(ap), g.AP[1], z, a_summed);
+  }
   if (threadIdx.x == 0) {
     const int ca = __ldcg(&g.fcnt[2 * z]), cb = __ldcg(&g.fcnt[2 * z + 1]);
     sm.na = ca;
@@ -353,7 +463,8 @@ static __device__ void resolve_plane(ResolveSmem& sm, const GridDev& g, const fl
 // collects what was changed, for the persistent kernel's repair).
 static __device__ void resolve_planes_into(ResolveSmem& sm, const GridDev& g, const float* uin, float* u, double* A,
                                            double* B, const double* ap, const double* bp, long long step,
-                                           DevCtrl* ctrl, abft_event* ev, unsigned long long* unresolved) {
+                                           DevCtrl* ctrl, abft_event* ev, unsigned long long* unresolved,
+                                           bool a_summed = false) {
   if (threadIdx.x == 0) sm.nfix = 0;
   __syncthreads();
   for (int zb = 0; zb < g.nz; zb += 1024) {
@@ -362,7 +473,7 @@ static __device__ void resolve_planes_into(ResolveSmem& sm, const GridDev& g, co
       sm.flag[j] = (__ldcg(&g.fcnt[2 * (zb + j)]) | __ldcg(&g.fcnt[2 * (zb + j) + 1])) != 0;
     __syncthreads();
     for (int j = 0; j < zn; ++j)
-      if (sm.flag[j]) resolve_plane(sm, g, uin, u, A, B, ap, bp, step, ctrl, ev, unresolved, zb + j);
+      if (sm.flag[j]) resolve_plane(sm, g, uin, u, A, B, ap, bp, step, ctrl, ev, unresolved, zb + j, a_summed);
     __syncthreads();
   }
 }
@@ -507,10 +618,11 @@ __device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, i
 // Entries of warps wbase, wbase + wstride, ... (32 consecutive entries each, below n)
 // checked by the calling warp; no block-wide synchronisation.
 template <int ACC>
-__device__ __forceinline__ void check_warps(const GridDev& g, int in, int out, int wbase, int wstride, int n) {
+__device__ __forceinline__ void check_warps(const GridDev& g, int in, int out, int wbase, int wstride, int first,
+                                            int n) {
   const InterpW w(g.k);
   const int lane = threadIdx.x & 31;
-  for (int base = wbase * 32; base < n; base += wstride * 32)
+  for (int base = first + wbase * 32; base < n; base += wstride * 32)
     if (base + lane < n) check_lane<ACC>(g, w, in, out, base + lane);
 }
 
@@ -528,8 +640,10 @@ __host__ __device__ inline int check_box_bytes(int nty, int ntx, int acc) {
   return kCheckBox * per * esz * (nty > ntx ? nty : ntx);
 }
 
+// rounds of one check: the a rounds (nz * ceil(nx/32)) then the b rounds; with one
+// checksum vector (Sec. 3.2) only the b rounds
 __device__ __forceinline__ int check_rounds_of(const GridDev& g) {
-  return g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
+  return g.nz * ((g.vec == 1 ? 0 : (g.nx + kCheckBox - 1) / kCheckBox) + (g.ny + kCheckBox - 1) / kCheckBox);
 }
 
 // One round of the boxed online check: 32 consecutive entries of a[z][.] or b[z][.]
@@ -545,6 +659,7 @@ __device__ __forceinline__ CheckRound check_round_at(const GridDev& g, int round
   CheckRound r;
   const int nxb = (g.nx + kCheckBox - 1) / kCheckBox;
   const int ra = g.nz * nxb;
+  if (g.vec == 1) round += ra;  // b rounds only
   r.is_a = round < ra;
   if (r.is_a) {
     r.z = round / nxb;

@@ -29,7 +29,7 @@ namespace {
 constexpr size_t kScratchBytes = 8u << 20;
 constexpr int kMaxDevices = 64;
 constexpr int kStaticTy = 16;
-constexpr size_t kCtrlBytes = 256;  // DevCtrl + DevGridCtrl, kept at the front of the array
+constexpr size_t kCtrlBytes = 1024;  // DevCtrl + DevGridCtrl, kept at the front of the array
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -146,7 +146,8 @@ __device__ void repair_next(const GridDev& g, const float* u_s, float* u_n, void
       const int r = t % (nyy * ntx);
       recompute_pb<ACC>(g, u_n, PB, tx0 + r % ntx, z, lo[1] + r / ntx);
     }
-    // column partials: one thread per (z, x, tile-y)
+    // column partials: one thread per (z, x, tile-y); none with one checksum vector
+    if (g.vec == 1) continue;
     const int xa = lo[2], xb = hi[2];
     const int ncols = (hi[0] - lo[0] + 1) * (xb - xa + 1) * (ty1 - ty0 + 1);
     for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
@@ -166,7 +167,7 @@ __device__ void repair_next(const GridDev& g, const float* u_s, float* u_n, void
 // thread at 96 registers; a 112-register cap left one CTA per SM (measured 3.4x slower).
 constexpr int kOnlineThreads = kSweepThreads + 32;
 
-template <class Tiles, int TY, int ACC>
+template <class Tiles, int TY, int ACC, int VEC = 2>
 __global__ void __launch_bounds__(kOnlineThreads, 2)
     k_persist_online(const __grid_constant__ PersistArgs a, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev,
                      DevSched sched) {
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
   const bool resident_c = (int)gridDim.x >= ntiles;
   const bool sweeper = threadIdx.x < kSweepThreads;
   // the check warp's rounds and its shared-memory box (after the tiles' shared memory)
-  const int rounds = g.nz * ((g.nx + kCheckBox - 1) / kCheckBox + (g.ny + kCheckBox - 1) / kCheckBox);
+  const int rounds = check_rounds_of(g);
   const int r0 = (int)((long long)rounds * blockIdx.x / gridDim.x);
   const int r1 = (int)((long long)rounds * (blockIdx.x + 1) / gridDim.x);
   unsigned char* craw = smem_raw + Tiles::smem_bytes(g.nz);  // past the tiles' region
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
       if (sweep)
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
           tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, !resident_c || k == 0);
-          tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[cur], g.u[nxt], tile % g.ntx, tile / g.ntx,
+          tiles.template run<true, ACC, VEC>(&a.tm_u[cur], &a.tm_c, g, g.u[cur], g.u[nxt], tile % g.ntx, tile / g.ntx,
                                         ctrl, pb_nxt);
         }
     } else if (check) {
@@ -229,10 +230,20 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
     if (!ok || !check) continue;
     // rare: locate, correct, repair the speculative sweep
     if (total != 0) {
+      // one-vector checks: every CTA sums a share of the columns the location needs (the
+      // other kernels leave it to the location step's block)
+      constexpr bool summed = VEC == 1;
+      if (summed) {
+        demand_sums(g, g.u[prv], g.u[cur], g.A[cur], g.AP[1], blockIdx.x, gridDim.x);
+        unsigned none = 0;
+        ok = grid_barrier_sum(bars, nbar++, nullptr, ctrl, &none);
+        if (!ok) continue;
+      }
       if (blockIdx.x == 0) {
         // u^s is the output of sweep s - 1; u^{s+1} that of sweep s
         resolve_planes_into(rs, g, g.u[prv], g.u[cur], g.A[cur], g.B[cur], g.AP[0], g.BP[0], s - 1, ctrl, ev,
-                            &g.gc->unresolved);
+                            &g.gc->unresolved, summed);
+        if (summed && threadIdx.x == 0) g.gc->nbz = 0;  // the plane list is consumed
         __syncthreads();
         // a targeted repair by this block only while it is smaller than a few tiles'
         // work; beyond that every CTA recomputes its tiles of the speculative sweep
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(kOnlineThreads, 2)
         if (sweeper)
           for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             tiles.issue(&a.tm_u[cur], &a.tm_c, g, tile % g.ntx, tile / g.ntx, s, ctrl, sched, !resident_c);
-            tiles.template run<true, ACC>(&a.tm_u[cur], &a.tm_c, g, g.u[cur], g.u[nxt], tile % g.ntx,
+            tiles.template run<true, ACC, VEC>(&a.tm_u[cur], &a.tm_c, g, g.u[cur], g.u[nxt], tile % g.ntx,
                                           tile / g.ntx, ctrl, pb_nxt);
           }
         unsigned none = 0;
@@ -427,9 +438,9 @@ static cudaError_t launch_offline_ty(const Launch& L, const PersistArgs& a, int*
   }
 }
 
-template <class Tiles, int TY, bool PROT, int ACC>
+template <class Tiles, int TY, bool PROT, int ACC, int VEC = 2>
 static cudaError_t launch_persist_t(const Launch& L, const PersistArgs& a, int* blocks_out) {
-  auto kern = PROT ? k_persist_online<Tiles, TY, ACC> : k_persist_plain<Tiles>;
+  auto kern = PROT ? k_persist_online<Tiles, TY, ACC, VEC> : k_persist_plain<Tiles>;
   const int smem = Tiles::smem_bytes(a.g.nz) + (PROT ? check_smem(a.g, ACC) : 0);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -463,7 +474,9 @@ static cudaError_t launch_persist_ty(const Launch& L, const PersistArgs& a, bool
   switch (a.g.acc) {
     case ABFT_ACC_TWOSUM: return launch_persist_t<Tiles, TY, true, ABFT_ACC_TWOSUM>(L, a, blocks);
     case ABFT_ACC_FP64: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP64>(L, a, blocks);
-    default: return launch_persist_t<Tiles, TY, true, ABFT_ACC_FP32>(L, a, blocks);
+    default:
+      return a.g.vec == 1 ? launch_persist_t<Tiles, TY, true, ABFT_ACC_FP32, 1>(L, a, blocks)
+                          : launch_persist_t<Tiles, TY, true, ABFT_ACC_FP32>(L, a, blocks);
   }
 }
 

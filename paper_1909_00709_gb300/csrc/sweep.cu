@@ -22,7 +22,7 @@ namespace abft {
 
 // One sweep of one grid: one CTA per tile.  The last CTA to finish commits the sweep
 // by advancing the grid's step counter (it drives injection and event stamps).
-template <class Tiles, bool PROT, int ACC>
+template <class Tiles, bool PROT, int ACC, int VEC = 2>
 __global__ void __launch_bounds__(256, 2)
     k_sweep(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c,
             const GridDev g, const float* __restrict__ uin, float* __restrict__ uout, DevCtrl* __restrict__ ctrl,
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256, 2)
   const long long step = g.gc->step;
   const int txi = blockIdx.x % g.ntx, tyi = blockIdx.x / g.ntx;
   tiles.issue(&tm_u, &tm_c, g, txi, tyi, step, ctrl, sched, true);
-  tiles.template run<PROT, ACC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
+  tiles.template run<PROT, ACC, VEC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&g.gc->done_sweep, 1u);
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256, 2)
 // tile, streamed as the sweep streams it.  The last CTA clears the flag.
 constexpr int kRedoPlanes = 8;  // above this many planes a tile is streamed again
 
-template <class Tiles, int TY, int ACC>
+template <class Tiles, int TY, int ACC, int VEC = 2>
 __global__ void __launch_bounds__(256, 2)
     k_redo_tiles(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c, const GridDev g,
                  const float* __restrict__ uin, float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256, 2)
       }
       __syncthreads();
       tiles.issue(&tm_u, &tm_c, g, txi, tyi, step, ctrl, sched, true);
-      tiles.template run<true, ACC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
+      tiles.template run<true, ACC, VEC>(&tm_u, &tm_c, g, uin, uout, txi, tyi, ctrl, 0);
     } else {
       const int ncol = min(kTX, g.nx - x0), nrow = min(TY, g.ny - y0);
       // this sweep's flips inside the tile, gathered once
@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(256, 2)
         uout[((size_t)z * g.ny + y) * g.px + x] = v;
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < npl * kTX; i += blockDim.x)
-        Tiles::template recompute_col<ACC>(g, uout, g.PA, tyi, zl + i / kTX, x0 + i % kTX);
+      if (VEC == 2)
+        for (int i = threadIdx.x; i < npl * kTX; i += blockDim.x)
+          Tiles::template recompute_col<ACC>(g, uout, g.PA, tyi, zl + i / kTX, x0 + i % kTX);
       for (int w = threadIdx.x >> 5; w < npl * nrow; w += blockDim.x >> 5)
         recompute_pb<ACC>(g, uout, g.PB, txi, zl + w / nrow, y0 + w % nrow);
     }
@@ -151,10 +152,10 @@ int sweep_smem_bytes(int ty, bool) {
   }
 }
 
-template <class Tiles, bool PROT, int ACC>
+template <class Tiles, bool PROT, int ACC, int VEC = 2>
 static cudaError_t launch_t(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
                             int in, int out) {
-  auto kern = k_sweep<Tiles, PROT, ACC>;
+  auto kern = k_sweep<Tiles, PROT, ACC, VEC>;
   const int smem = Tiles::smem_bytes(g.nz);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -169,7 +170,9 @@ static cudaError_t launch_tiles(const Launch& L, const GridDev& g, const CUtenso
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: return launch_t<Tiles, true, ABFT_ACC_TWOSUM>(L, g, tm_in, tm_c, in, out);
     case ABFT_ACC_FP64: return launch_t<Tiles, true, ABFT_ACC_FP64>(L, g, tm_in, tm_c, in, out);
-    default: return launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, in, out);
+    default:
+      return g.vec == 1 ? launch_t<Tiles, true, ABFT_ACC_FP32, 1>(L, g, tm_in, tm_c, in, out)
+                        : launch_t<Tiles, true, ABFT_ACC_FP32>(L, g, tm_in, tm_c, in, out);
   }
 }
 
@@ -203,6 +206,7 @@ static cudaError_t redo_t(const Launch& L, const GridDev& g, const CUtensorMap& 
   const int blocks = g.ntx * g.nty, smem = Tiles::smem_bytes(g.nz);
   auto kern = g.acc == ABFT_ACC_TWOSUM ? k_redo_tiles<Tiles, TY, ABFT_ACC_TWOSUM>
               : g.acc == ABFT_ACC_FP64 ? k_redo_tiles<Tiles, TY, ABFT_ACC_FP64>
+              : g.vec == 1             ? k_redo_tiles<Tiles, TY, ABFT_ACC_FP32, 1>
                                        : k_redo_tiles<Tiles, TY, ABFT_ACC_FP32>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -358,7 +358,9 @@ __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __
   }
 }
 
-template <int TY, bool PROT, int ACC, bool CLAMPED>
+// VEC: checksum vectors of the epilogue (2: a and b partials; 1: b partials only, for
+// the one-vector online check of Sec. 3.2)
+template <int TY, bool PROT, int ACC, bool CLAMPED, int VEC = 2>
 __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
                                                const float* __restrict__ uin, float* __restrict__ uout, int txi, int tyi,
                                                DevCtrl* __restrict__ ctrl, const SweepSmem<TY>& sm, unsigned& seq,
@@ -387,6 +389,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
   const bool full = x0 + kTX <= g.nx && y0 + TY <= g.ny;  // no ragged edge in this tile
   // FP32 partials: lane partials through shared memory, reduced by one warp per plane
   constexpr bool SMEM_EPI = ACC == ABFT_ACC_FP32;
+  constexpr bool PA_ON = PROT && VEC == 2;  // column partials (the a vector)
   static_assert(NW * kTX * 4 + TY * kRowPitch * 4 <= Cfg::RED_HALF, "FP32 epilogue buffer");
 
   for (int z = 0; z < nz; ++z) {
@@ -399,7 +402,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
     unsigned char* red = sm.red + (z & 1) * Cfg::RED_HALF;
     float* rowp = reinterpret_cast<float*>(red + NW * kTX * 4);  // FP32 epilogue: [TY][kRowPitch] lane partials
     AccA<ACC> acc;
-    if (PROT) acc.zero();
+    if (PA_ON) acc.zero();
     typename RowPart<ACC>::T rp[Cfg::RPW > 1 ? Cfg::RPW : 2];
 #pragma unroll
     for (int rr = 0; rr < Cfg::RPW; ++rr) {
@@ -453,7 +456,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
         if (SMEM_EPI) rowp[r * kRowPitch + lane] = ((m[0] + m[1]) + m[2]) + m[3];  // RowPart<FP32>::of
         else if (Cfg::RPW == 1) AccA<ACC>::row_store(m, PB, ((size_t)txi * nz + z) * g.pb_stride + y, yv && lane == 0);
         else rp[rr] = RowPart<ACC>::of(m);
-        acc.add(m);
+        if (PA_ON) acc.add(m);
       }
     }
     if (PROT && !SMEM_EPI && Cfg::RPW > 1) {  // this warp's rows reduced together; lane (rr << SH) holds row rr
@@ -463,7 +466,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny)
         RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.pb_stride + y, tot);
     }
-    if (PROT) acc.put(sm.red + (z & 1) * Cfg::RED_HALF, warp, lane);
+    if (PA_ON) acc.put(sm.red + (z & 1) * Cfg::RED_HALF, warp, lane);
     tile_sync();
     if (tid == 0 && z >= 1 && z - 1 + S < nz) {
       fence_proxy_async();
@@ -473,7 +476,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       // two warps per plane (rotating with z) reduce the plane's partials: one sums four
       // columns per lane over the eight warps in order, the other row `lane` over its 32
       // lane partials by the butterfly's own pairing (the same sums as row_store)
-      if (warp == (z & (NW - 1))) {
+      if (PA_ON && warp == (z & (NW - 1))) {
         const float* r = reinterpret_cast<const float*>(red);
         float4 c = reinterpret_cast<const float4*>(r)[lane];
 #pragma unroll
@@ -498,7 +501,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
           static_cast<float*>(PB)[((size_t)txi * nz + z) * g.pb_stride + y0 + lane] = t[0];
         }
       }
-    } else if (PROT && tid < kTX) {
+    } else if (PA_ON && tid < kTX) {
       AccA<ACC>::template column_store<NW>(sm.red + (z & 1) * Cfg::RED_HALF, tid, PA,
                                            ((size_t)tyi * nz + z) * g.pa_stride + x0 + tid);
     }
@@ -663,7 +666,7 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
   tile_sync();
 }
 
-template <int TY, bool PROT, int ACC, bool CLAMPED>
+template <int TY, bool PROT, int ACC, bool CLAMPED, int VEC = 2>
 __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* __restrict__ uin,
                                                  float* __restrict__ uout, int txi, int tyi,
                                                  DevCtrl* __restrict__ ctrl, const ShallowSmem<TY>& sm,
@@ -681,6 +684,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
   const int last = g.nx - 1 - gx0;
   const bool full = x0 + kTX <= g.nx && y0 + TY <= g.ny;  // no ragged edge in this tile
   constexpr int PLANE = (TY + 2) * kUW;
+  constexpr bool PA_ON = PROT && VEC == 2;  // column partials (the a vector)
   for (int z = warp; z < nz; z += NW) {
     const float* Uz = sm.u + z * PLANE;
     // at a z face: the centre plane, or for periodic boundaries the staged opposite face
@@ -689,7 +693,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
     const float* Ut = z + 1 < nz ? Uz + PLANE : (wrap ? sm.u : Uz);
     const float* Cz = sm.c + z * TY * kTX;
     AccA<ACC> acc;
-    if (PROT) acc.zero();
+    if (PA_ON) acc.zero();
     typename RowPart<ACC>::T rp[TY];
 #pragma unroll
     for (int r = 0; r < TY; ++r) {
@@ -740,11 +744,11 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
 #pragma unroll
         for (int i = 0; i < 4; ++i) m[i] = full ? v[i] : ((yv && i <= last) ? v[i] : 0.f);
         rp[r] = RowPart<ACC>::of(m);
-        acc.add(m);
+        if (PA_ON) acc.add(m);
       }
     }
     if (PROT) {
-      acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
+      if (PA_ON) acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
       const typename RowPart<ACC>::T tot = reduce_rows<ACC, TY>(rp, lane);
       constexpr int SH = TY == 8 ? 2 : 1;  // lane l holds row l >> SH
       const int r = lane >> SH, y = y0 + r;
@@ -800,10 +804,10 @@ struct StreamTiles {
                         long long step, DevCtrl* ctrl, const DevSched& sched, bool) {
     sweep_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, seq);
   }
-  template <bool PROT, int ACC>
+  template <bool PROT, int ACC, int VEC = 2>
   __device__ __forceinline__ void run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
                                       const float* uin, float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
-    sweep_tile_run<TY, PROT, ACC, CL>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, sm, seq, pbuf);
+    sweep_tile_run<TY, PROT, ACC, CL, VEC>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, sm, seq, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
@@ -826,10 +830,10 @@ struct ShallowTiles {
                         long long step, DevCtrl* ctrl, const DevSched& sched, bool load_c) {
     shallow_tile_issue<TY>(tm_u, tm_c, g, txi, tyi, step, ctrl, sched, sm, load_c);
   }
-  template <bool PROT, int ACC>
+  template <bool PROT, int ACC, int VEC = 2>
   __device__ __forceinline__ void run(const CUtensorMap*, const CUtensorMap*, const GridDev& g, const float* uin,
                                       float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
-    shallow_tile_run<TY, PROT, ACC, CL>(g, uin, uout, txi, tyi, ctrl, sm, phase, pbuf);
+    shallow_tile_run<TY, PROT, ACC, CL, VEC>(g, uin, uout, txi, tyi, ctrl, sm, phase, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {

@@ -353,3 +353,49 @@ def test_schedule_statistics(orc):
     np.testing.assert_array_equal(many, again)
     assert len(orc.schedule(7, 0.0, 0xFFFFFFFF, shape, 0, 100)) == 0
     assert len(orc.schedule(7, 1.0, 0, shape, 0, 100)) == 0
+
+
+# ------------------------------------------- one-vector detection (Sec. 3.2)
+
+def test_one_vector_square_grid_finds_the_same_events(orc):
+    """On a square plane both vectors sum the same number of points, so a flip that moves
+    a past its threshold moves b past it too: testing b alone (and a only where b failed)
+    finds exactly the events of testing both, for every bit."""
+    st, C, temp = hotspot(orc, (64, 64, 8), 1)
+    rng = np.random.default_rng(5)
+    fl = inputs.flip_list([(2 + k, 0, int(rng.integers(8)), int(rng.integers(64)), int(rng.integers(64)), k)
+                           for k in range(32)])
+    both = orc.run(st, C, temp, 40, orc.MODE_ONLINE, fl)
+    one = orc.run(st, C, temp, 40, orc.MODE_ONLINE, fl, vectors=1)
+    key = lambda r: sorted((int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"]))
+                           for e in r["events"])
+    assert key(both) == key(one) and len(key(one)) == 19  # bits 13..31
+    np.testing.assert_array_equal(both["u"], one["u"])
+
+
+@pytest.mark.parametrize("bit", range(12, 24))
+def test_one_vector_detects_by_the_b_threshold(orc, bit):
+    """A non-square plane (nx = 200, ny = 37): b sums 200 points, a only 37, so b's
+    threshold eps |b| is higher.  With one vector a flip of size |delta| is found iff
+    |delta| > eps |b[z][y]| (the b entry of its row, from the fault-free grid), whatever
+    a would say; with both vectors iff it exceeds eps |a| or eps |b|."""
+    shape, t, z, y, x = (200, 37, 5), 6, 2, 20, 150
+    st, C, temp = hotspot(orc, shape, 7)
+    pre = orc.run(st, C, temp, t, orc.MODE_NONE)["u"]       # u^t
+    post = orc.run(st, C, pre, 1, orc.MODE_NONE)["u"]       # u^{t+1}, fault-free
+    v = np.float32(post[z, y, x])
+    flipped = (np.array([v]).view(np.uint32) ^ np.uint32(1 << bit)).view(np.float32)[0]
+    delta = abs(float(flipped) - float(v))
+    ta = 1e-5 * abs(post[z, :, x].sum())
+    tb = 1e-5 * abs(post[z, y, :].sum())
+    assert ta < tb
+    margin = lambda d, th: abs(d / th - 1.0) > 0.05  # clear of the guard band
+    if not (margin(delta, ta) and margin(delta, tb)):
+        pytest.skip("flip size inside the guard band")
+    fl = inputs.flip_list([(t, 0, z, y, x, bit)])
+    one = orc.run(st, C, temp, t + 2, orc.MODE_ONLINE, fl, vectors=1)
+    both = orc.run(st, C, temp, t + 2, orc.MODE_ONLINE, fl)
+    assert (one["n_events"] > 0) == (delta > tb)
+    assert (both["n_events"] > 0) == (delta > ta)
+    if ta < delta <= tb:  # seen by a alone: both vectors recompute its column
+        assert [(int(e["y"]), int(e["x"]), int(e["kind"])) for e in both["events"]] == [(-1, x, orc.EV_RECOMPUTED)]
