@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--sweeps", type=int, default=None, help="sweeps per job for --profile captures")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
                    help="abft_options field for --profile captures (e.g. tile_y=16)")
+    p.add_argument("--vectors", type=int, default=1, choices=[1, 2],
+                   help="checksum vectors of the online check: 1 = b every sweep, a where b failed "
+                        "(the paper's recommendation, Sec. 3.2); 2 = both every sweep")
     return p.parse_args()
 
 
@@ -121,7 +124,7 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def oracle_sample(sweeps: int):
+def oracle_sample(sweeps: int, vectors: int = 1):
     """The FP64 oracle on the same workload for `sweeps` online sweeps (single thread)."""
     import oracle
     from paper_1909_00709_gb300 import inputs
@@ -132,7 +135,7 @@ def oracle_sample(sweeps: int):
     C = oracle.source_term(power, co)
     sched = oracle.schedule(1, RATE, 0xFFFFFFFF, SHAPE, 0, sweeps)
     t0 = time.perf_counter()
-    oracle.run(st, C, temp, sweeps, oracle.MODE_ONLINE, sched)
+    oracle.run(st, C, temp, sweeps, oracle.MODE_ONLINE, sched, vectors=vectors)
     return time.perf_counter() - t0
 
 
@@ -146,8 +149,8 @@ def run_reference(args, rank, world):
         return
     per = 20
     for _ in range(args.warmup):
-        oracle_sample(per)
-    ts = [oracle_sample(per) for _ in range(args.steps)]
+        oracle_sample(per, args.vectors)
+    ts = [oracle_sample(per, args.vectors) for _ in range(args.steps)]
     tot = sum(ts)
     glups = n_points() * per * args.steps / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": args.gpus,
@@ -155,7 +158,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": per, "mode": "online",
-                       "flip_rate_per_sweep": RATE},
+                       "flip_rate_per_sweep": RATE, "checksum_vectors": args.vectors},
             "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per} online sweeps of the {WORKLOAD} workload per step"},
             "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -198,14 +201,18 @@ def run_ours(args, rank, world, local):
             total += e0.elapsed_time(e1)
         return total
 
-    prot = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
+    prot = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream, vectors=args.vectors)
     prot.inject(1, RATE, 0xFFFFFFFF)
+    # the other checksum-vector setting, timed beside it
+    prot2 = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream, vectors=3 - args.vectors)
+    prot2.inject(1, RATE, 0xFFFFFFFF)
     plain = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
     off = abi.Context([SHAPE], [temp], [power], [co], device=dev, stream=stream)
     off.inject(1, RATE, 0xFFFFFFFF)
 
     for _ in range(args.warmup):
         prot.step(SWEEPS, abi.MODE_ONLINE)
+        prot2.step(SWEEPS, abi.MODE_ONLINE)
         plain.step(SWEEPS, abi.MODE_NONE)
         off.step(SWEEPS, abi.MODE_OFFLINE)
     torch.cuda.synchronize(dev)
@@ -221,6 +228,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     ms_plain = timed_jobs(plain, abi.MODE_NONE, args.steps)
     ms_off = timed_jobs(off, abi.MODE_OFFLINE, args.steps)
+    ms_prot2 = timed_jobs(prot2, abi.MODE_ONLINE, args.steps)
     events = prot.events()
     off_cnt = off.counters()
     side = side_runs(dev, stream, flush) if (rank == 0 and not args.no_side) else None
@@ -252,7 +260,8 @@ def run_ours(args, rank, world, local):
         for k in range(args.warmup + args.steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            with abi.Context([SHAPE], [host_t], [host_p], [co], device=dev, stream=stream) as c:
+            with abi.Context([SHAPE], [host_t], [host_p], [co], device=dev, stream=stream,
+                             vectors=args.vectors) as c:
                 c.inject(1, RATE, 0xFFFFFFFF)
                 c.step(SWEEPS, abi.MODE_ONLINE)
                 c.read(0, out=host_out)
@@ -273,7 +282,7 @@ def run_ours(args, rank, world, local):
     cpu = None
     if not args.no_cpu and world == 1:
         sweeps = 200
-        t = oracle_sample(sweeps)
+        t = oracle_sample(sweeps, args.vectors)
         cpu = {"value": n_points() * sweeps / t / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
                "sample": f"{sweeps} online sweeps of the {WORKLOAD} workload (seeded flips, 1e-3/sweep)"}
     line = {
@@ -282,9 +291,13 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": SWEEPS, "mode": "online",
                    "flip_rate_per_sweep": RATE, "eps": 1e-5, "checksum_acc": "fp32-tile/fp64",
+                   "checksum_vectors": args.vectors,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": "replicas"},
         "overhead_pct": (ms_prot / ms_plain - 1.0) * 100.0,
         "unprotected_glups": plain_glups,
+        f"online_{3 - args.vectors}_vectors": {
+            "glups": n_points() * SWEEPS * args.steps / (ms_prot2 / 1e3) / 1e9,
+            "overhead_pct": (ms_prot2 / ms_plain - 1.0) * 100.0},
         "offline": {"glups": off_glups, "overhead_pct": (ms_off / ms_plain - 1.0) * 100.0, "delta": 16,
                     "rollbacks": off_cnt["rollbacks"]},
         "events": {"corrected": int((events["kind"] == 1).sum()), "recomputed": int((events["kind"] == 2).sum())},
@@ -302,7 +315,7 @@ def run_ours(args, rank, world, local):
         line.update(side)
         line["large"]["roofline_frac"] = {k: v * BYTES_PER_UPDATE / peak for k, v in side["large"]["glups"].items()}
     print(json.dumps(line), flush=True)
-    for c in (prot, plain, off):
+    for c in (prot, prot2, plain, off):
         c.close()
 
 
@@ -503,7 +516,7 @@ def run_profile(args, local):
     temp, power = inputs.grid_inputs(*SHAPE, seed=1)
     co = inputs.hotspot_coeffs(*SHAPE)
     opts = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
-    prot = abi.Context([SHAPE], [temp], [power], [co], **opts)
+    prot = abi.Context([SHAPE], [temp], [power], [co], **{"vectors": args.vectors, **opts})
     prot.inject(1, RATE, 0xFFFFFFFF)
     plain = abi.Context([SHAPE], [temp], [power], [co], **opts)
     for _ in range(args.warmup):
