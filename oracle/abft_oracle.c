@@ -363,9 +363,12 @@ static void inject(const orc_stencil* s, const orc_flip* flips, int64_t nflips, 
 static int alpha_beta_vanish(const orc_stencil* s) {
   if (s->boundary == ORC_PERIODIC) return 1;
   if (s->boundary == ORC_ZERO) return 0;
-  /* clamped: every point (i, j, k) needs a partner (i, -j, k) and (-i, j, k) of equal weight */
+  /* clamped: every point (i, j, k) needs a partner (i, -j, k) and (-i, j, k) of equal weight,
+     and in-plane offsets of at most one: for |j| = 2 the clamped terms of Theorem 1 are
+     2 u_0 - u_{n-2} - u_{n-1} and 2 u_{n-1} - u_0 - u_1, whose sum does not vanish */
   for (int k = 0; k < s->npts; k++) {
     const orc_point* p = &s->pts[k];
+    if (abs(p->dx) > 1 || abs(p->dy) > 1) return 0;
     int mirror_y = 0, mirror_x = 0;
     for (int m = 0; m < s->npts; m++) {
       const orc_point* q = &s->pts[m];

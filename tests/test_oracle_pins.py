@@ -332,6 +332,30 @@ def test_offline_refuses_nonvanishing_boundary_terms(orc):
         orc.run(st, np.zeros_like(u), u, 4, orc.MODE_OFFLINE, delta=2)
 
 
+def test_clamped_radius_two_terms_do_not_vanish(orc):
+    """A symmetric 13-point star under clamped boundaries: the simple form of Eq. (6)/(7)
+    misses the terms of Theorem 1 (exact integer arithmetic shows the gap), so the
+    offline chain, which needs them to vanish, is refused; periodic boundaries accept it."""
+    pts = [(0, 0, 0, 4.0)] + [(d * s, 0, 0, 1.0) for d in (1, 2) for s in (-1, 1)] + \
+          [(0, d * s, 0, 1.0) for d in (1, 2) for s in (-1, 1)] + [(0, 0, s, 1.0) for s in (-1, 1)]
+    shape = (9, 7, 3)
+    u = int_grid(shape, 4)
+    C = np.zeros_like(u)
+    st = orc.Stencil(shape, pts, CLAMP)
+    out = orc.sweep(st, C, u)
+    a_true, b_true = orc.checksums(out)
+    a0, b0 = orc.checksums(u)
+    ap, bp = orc.interpolate_simple(st, *orc.checksums(C), a0, b0)
+    assert np.abs(ap - a_true).max() > 0 and np.abs(bp - b_true).max() > 0
+    ap, bp = orc.interpolate(st, *orc.checksums(C), a0, b0, u)
+    np.testing.assert_array_equal(ap, a_true)
+    np.testing.assert_array_equal(bp, b_true)
+    with pytest.raises(RuntimeError):
+        orc.run(st, C, u, 4, orc.MODE_OFFLINE, delta=2)
+    per = orc.Stencil(shape, pts, PERIODIC)
+    assert orc.run(per, C, u, 4, orc.MODE_OFFLINE, delta=2)["n_events"] == 0
+
+
 # ----------------------------------------------------------- flip schedule
 
 def test_splitmix64_published_first_output(orc, golden):
