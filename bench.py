@@ -39,7 +39,7 @@ BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) of one 200-sweep launch of the dominant kernel, from one ncu
 # capture of this build (the working set stays in L2); None for kernels not captured
-TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 16993792 + 301824}
+TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 16928768 + 96512}
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
