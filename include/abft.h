@@ -252,7 +252,8 @@ ABFT_API const char* abft_status_string(abft_status s);
    base->stream; `sweeps` (1..100000) are timed after 2 warm-up sweeps. *best receives
    *base with tile_y, shallow, persistent and batch set to the winner's;
    *best_us_per_sweep its time. Results are cached per (shapes, mode, acc, delta,
-   sweeps, track_residual) for the process: a repeated call returns at once.
+   sweeps, track_residual, boundary, vectors) for the process: a repeated call returns
+   at once.
    Errors: ABFT_E_INVAL (arguments), ABFT_E_NOMEM (no candidate fits the workspace),
    or the first failing call's status. */
 ABFT_API size_t abft_tune_workspace_bytes(const abft_grid* grids, int32_t n_grids, const abft_options* base);

@@ -38,7 +38,8 @@ std::map<std::string, Result> g_cache;
 std::string key_of(const abft_grid* g, int n, const abft_options* o, int mode, int sweeps) {
   std::string k;
   char b[96];
-  snprintf(b, sizeof b, "m%d a%d d%d s%d t%d b%d|", mode, o->acc, o->delta, sweeps, o->track_residual, o->boundary);
+  snprintf(b, sizeof b, "m%d a%d d%d s%d t%d b%d v%d|", mode, o->acc, o->delta, sweeps, o->track_residual,
+           o->boundary, o->vectors);
   k += b;
   for (int i = 0; i < n; ++i) {
     snprintf(b, sizeof b, "%d,%d,%d;", g[i].nx, g[i].ny, g[i].nz);

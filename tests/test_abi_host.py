@@ -64,6 +64,11 @@ def test_workspace_bytes_validates(abi):
         assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=bc)) > 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=3)) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=-1)) == 0
+    # checksum vectors of the online check: 2 (default) or 1; the field after `boundary`
+    assert o.vectors == 2
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(vectors=1)) > 0
+    for bad in (0, 3):
+        assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(vectors=bad)) == 0
     big = abi.abft_workspace_bytes([(1024, 1024, 256)], o)
     assert big > 4 * 1024 * 1024 * 256 * 4
     two = abi.abft_workspace_bytes([(64, 64, 8), (100, 37, 5)], o)
