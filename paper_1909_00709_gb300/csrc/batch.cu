@@ -201,26 +201,29 @@ static cudaError_t dispatch_acc(bool prep, const Launch* L, const BatchArgs* a, 
   }
 }
 
-template <bool CL>
-static cudaError_t dispatch_cl(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
+template <int BC>
+static cudaError_t dispatch_bc(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
                                bool prot, int acc) {
   if (shallow) {
-    if (ty == 16) return dispatch_acc<ShallowTiles<16, CL>>(prep, L, a, blocks, smem, prot, acc);
-    if (ty == 8) return dispatch_acc<ShallowTiles<8, CL>>(prep, L, a, blocks, smem, prot, acc);
+    if (ty == 16) return dispatch_acc<ShallowTiles<16, BC>>(prep, L, a, blocks, smem, prot, acc);
+    if (ty == 8) return dispatch_acc<ShallowTiles<8, BC>>(prep, L, a, blocks, smem, prot, acc);
     return cudaErrorInvalidValue;
   }
   switch (ty) {
-    case 8: return dispatch_acc<StreamTiles<8, CL>>(prep, L, a, blocks, smem, prot, acc);
-    case 16: return dispatch_acc<StreamTiles<16, CL>>(prep, L, a, blocks, smem, prot, acc);
-    case 32: return dispatch_acc<StreamTiles<32, CL>>(prep, L, a, blocks, smem, prot, acc);
+    case 8: return dispatch_acc<StreamTiles<8, BC>>(prep, L, a, blocks, smem, prot, acc);
+    case 16: return dispatch_acc<StreamTiles<16, BC>>(prep, L, a, blocks, smem, prot, acc);
+    case 32: return dispatch_acc<StreamTiles<32, BC>>(prep, L, a, blocks, smem, prot, acc);
     default: return cudaErrorInvalidValue;
   }
 }
 
 static cudaError_t dispatch(bool prep, const Launch* L, const BatchArgs* a, int blocks, int smem, int shallow, int ty,
                             bool prot, int acc, int bc) {
-  return bc == ABFT_BC_CLAMP ? dispatch_cl<true>(prep, L, a, blocks, smem, shallow, ty, prot, acc)
-                             : dispatch_cl<false>(prep, L, a, blocks, smem, shallow, ty, prot, acc);
+  switch (bc) {
+    case ABFT_BC_PERIODIC: return dispatch_bc<ABFT_BC_PERIODIC>(prep, L, a, blocks, smem, shallow, ty, prot, acc);
+    case ABFT_BC_ZERO: return dispatch_bc<ABFT_BC_ZERO>(prep, L, a, blocks, smem, shallow, ty, prot, acc);
+    default: return dispatch_bc<ABFT_BC_CLAMP>(prep, L, a, blocks, smem, shallow, ty, prot, acc);
+  }
 }
 
 cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int bc, int smem) {

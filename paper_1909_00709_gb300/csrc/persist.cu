@@ -1,5 +1,6 @@
 // Persistent launches of grids with the clamped boundary (the default) and the public
-// entry points; grids with other boundary rules go to persist_bc.cu.
+// entry points; grids with other boundary rules go to persist_bc.cu (periodic) and
+// persist_zero.cu (empty).
 #include <cstring>
 
 #include "persist.cuh"
@@ -7,7 +8,9 @@
 namespace abft {
 
 bool persistent_fits(const GridDev& g, bool prot) {
-  return g.bc == ABFT_BC_CLAMP ? persistent_fits_cl<true>(g, prot) : persistent_fits_generic(g, prot);
+  return g.bc == ABFT_BC_PERIODIC ? persistent_fits_periodic(g, prot)
+         : g.bc == ABFT_BC_ZERO   ? persistent_fits_zero(g, prot)
+                                  : persistent_fits_cl<ABFT_BC_CLAMP>(g, prot);
 }
 
 cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3], const CUtensorMap& tm_c,
@@ -23,8 +26,9 @@ cudaError_t launch_persistent(const Launch& L, const GridDev& g, const CUtensorM
   a.first_in = first_in;
   a.p = p;
   a.q = q;
-  return g.bc == ABFT_BC_CLAMP ? launch_persistent_cl<true>(L, a, prot, blocks)
-                               : launch_persistent_generic(L, a, prot, blocks);
+  return g.bc == ABFT_BC_PERIODIC ? launch_persistent_periodic(L, a, prot, blocks)
+         : g.bc == ABFT_BC_ZERO   ? launch_persistent_zero(L, a, prot, blocks)
+                                  : launch_persistent_cl<ABFT_BC_CLAMP>(L, a, prot, blocks);
 }
 
 cudaError_t launch_persistent_offline(const Launch& L, const GridDev& g, const CUtensorMap tm_u[3],
@@ -39,11 +43,15 @@ cudaError_t launch_persistent_offline(const Launch& L, const GridDev& g, const C
   a.n_steps = n_steps;
   a.first_in = ck;
   a.delta = delta;
-  return g.bc == ABFT_BC_CLAMP ? launch_offline_cl<true>(L, a, blocks) : launch_offline_generic(L, a, blocks);
+  return g.bc == ABFT_BC_PERIODIC ? launch_offline_periodic(L, a, blocks)
+         : g.bc == ABFT_BC_ZERO   ? launch_offline_zero(L, a, blocks)
+                                  : launch_offline_cl<ABFT_BC_CLAMP>(L, a, blocks);
 }
 
 bool persistent_offline_fits(const GridDev& g) {
-  return g.bc == ABFT_BC_CLAMP ? offline_fits_cl<true>(g) : persistent_offline_fits_generic(g);
+  return g.bc == ABFT_BC_PERIODIC ? persistent_offline_fits_periodic(g)
+         : g.bc == ABFT_BC_ZERO   ? persistent_offline_fits_zero(g)
+                                  : offline_fits_cl<ABFT_BC_CLAMP>(g);
 }
 
 }  // namespace abft

@@ -1,5 +1,5 @@
 // Persistent cooperative kernels: many sweeps of one grid in one launch (kernels and
-// their launch helpers, included by persist.cu and persist_bc.cu).
+// their launch helpers, included by persist.cu, persist_bc.cu and persist_zero.cu).
 //
 // Every CTA stays resident for the whole run and owns a fixed set of 128 x TY tiles;
 // sweeps are separated by a grid barrier instead of a kernel boundary.
@@ -511,68 +511,72 @@ static bool offline_fits_t(const GridDev& g) {
   return (long long)g.ntx * g.nty <= (long long)per_sm * sms;
 }
 
-template <bool CL>
+template <int BC>
 static bool persistent_fits_cl(const GridDev& g, bool prot) {
   if (g.shallow)
-    return g.ty == 8 ? fits_t<ShallowTiles<8, CL>, 8>(g, prot) : fits_t<ShallowTiles<16, CL>, 16>(g, prot);
+    return g.ty == 8 ? fits_t<ShallowTiles<8, BC>, 8>(g, prot) : fits_t<ShallowTiles<16, BC>, 16>(g, prot);
   switch (g.ty) {
-    case 8: return fits_t<StreamTiles<8, CL>, 8>(g, prot);
-    case 16: return fits_t<StreamTiles<16, CL>, 16>(g, prot);
-    default: return fits_t<StreamTiles<32, CL>, 32>(g, prot);
+    case 8: return fits_t<StreamTiles<8, BC>, 8>(g, prot);
+    case 16: return fits_t<StreamTiles<16, BC>, 16>(g, prot);
+    default: return fits_t<StreamTiles<32, BC>, 32>(g, prot);
   }
 }
 
-template <bool CL>
+template <int BC>
 static cudaError_t launch_persistent_cl(const Launch& L, const PersistArgs& a, bool prot, int* blocks) {
   const GridDev& g = a.g;
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return launch_persist_ty<ShallowTiles<8, CL>, 8>(L, a, prot, blocks);
-      case 16: return launch_persist_ty<ShallowTiles<16, CL>, 16>(L, a, prot, blocks);
+      case 8: return launch_persist_ty<ShallowTiles<8, BC>, 8>(L, a, prot, blocks);
+      case 16: return launch_persist_ty<ShallowTiles<16, BC>, 16>(L, a, prot, blocks);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return launch_persist_ty<StreamTiles<8, CL>, 8>(L, a, prot, blocks);
-    case 16: return launch_persist_ty<StreamTiles<16, CL>, 16>(L, a, prot, blocks);
-    case 32: return launch_persist_ty<StreamTiles<32, CL>, 32>(L, a, prot, blocks);
+    case 8: return launch_persist_ty<StreamTiles<8, BC>, 8>(L, a, prot, blocks);
+    case 16: return launch_persist_ty<StreamTiles<16, BC>, 16>(L, a, prot, blocks);
+    case 32: return launch_persist_ty<StreamTiles<32, BC>, 32>(L, a, prot, blocks);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool CL>
+template <int BC>
 static cudaError_t launch_offline_cl(const Launch& L, const PersistArgs& a, int* blocks) {
   const GridDev& g = a.g;
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return launch_offline_ty<ShallowTiles<8, CL>, 8>(L, a, blocks);
-      case 16: return launch_offline_ty<ShallowTiles<16, CL>, 16>(L, a, blocks);
+      case 8: return launch_offline_ty<ShallowTiles<8, BC>, 8>(L, a, blocks);
+      case 16: return launch_offline_ty<ShallowTiles<16, BC>, 16>(L, a, blocks);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return launch_offline_ty<StreamTiles<8, CL>, 8>(L, a, blocks);
-    case 16: return launch_offline_ty<StreamTiles<16, CL>, 16>(L, a, blocks);
-    case 32: return launch_offline_ty<StreamTiles<32, CL>, 32>(L, a, blocks);
+    case 8: return launch_offline_ty<StreamTiles<8, BC>, 8>(L, a, blocks);
+    case 16: return launch_offline_ty<StreamTiles<16, BC>, 16>(L, a, blocks);
+    case 32: return launch_offline_ty<StreamTiles<32, BC>, 32>(L, a, blocks);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool CL>
+template <int BC>
 static bool offline_fits_cl(const GridDev& g) {
-  if (g.shallow) return g.ty == 8 ? offline_fits_t<ShallowTiles<8, CL>, 8>(g) : offline_fits_t<ShallowTiles<16, CL>, 16>(g);
+  if (g.shallow) return g.ty == 8 ? offline_fits_t<ShallowTiles<8, BC>, 8>(g) : offline_fits_t<ShallowTiles<16, BC>, 16>(g);
   switch (g.ty) {
-    case 8: return offline_fits_t<StreamTiles<8, CL>, 8>(g);
-    case 16: return offline_fits_t<StreamTiles<16, CL>, 16>(g);
-    default: return offline_fits_t<StreamTiles<32, CL>, 32>(g);
+    case 8: return offline_fits_t<StreamTiles<8, BC>, 8>(g);
+    case 16: return offline_fits_t<StreamTiles<16, BC>, 16>(g);
+    default: return offline_fits_t<StreamTiles<32, BC>, 32>(g);
   }
 }
 
-// The same launches for grids with a periodic or empty boundary (tile policies with
-// CL = false), compiled in their own translation unit.
-bool persistent_fits_generic(const GridDev& g, bool prot);
-cudaError_t launch_persistent_generic(const Launch& L, const PersistArgs& a, bool prot, int* blocks);
-cudaError_t launch_offline_generic(const Launch& L, const PersistArgs& a, int* blocks);
-bool persistent_offline_fits_generic(const GridDev& g);
+// The same launches for grids with a periodic (persist_bc.cu) or an empty boundary
+// (persist_zero.cu), each rule's kernels compiled in a translation unit of its own.
+bool persistent_fits_periodic(const GridDev& g, bool prot);
+cudaError_t launch_persistent_periodic(const Launch& L, const PersistArgs& a, bool prot, int* blocks);
+cudaError_t launch_offline_periodic(const Launch& L, const PersistArgs& a, int* blocks);
+bool persistent_offline_fits_periodic(const GridDev& g);
+bool persistent_fits_zero(const GridDev& g, bool prot);
+cudaError_t launch_persistent_zero(const Launch& L, const PersistArgs& a, bool prot, int* blocks);
+cudaError_t launch_offline_zero(const Launch& L, const PersistArgs& a, int* blocks);
+bool persistent_offline_fits_zero(const GridDev& g);
 
 }  // namespace abft

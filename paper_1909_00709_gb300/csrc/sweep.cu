@@ -176,28 +176,31 @@ static cudaError_t launch_tiles(const Launch& L, const GridDev& g, const CUtenso
   }
 }
 
-template <bool CL>
-static cudaError_t launch_sweep_cl(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
+template <int BC>
+static cudaError_t launch_sweep_bc(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
                                    const CUtensorMap& tm_c, int in, int out, bool prot) {
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return launch_tiles<ShallowTiles<8, CL>>(L, g, tm_in, tm_c, in, out, prot);
-      case 16: return launch_tiles<ShallowTiles<16, CL>>(L, g, tm_in, tm_c, in, out, prot);
+      case 8: return launch_tiles<ShallowTiles<8, BC>>(L, g, tm_in, tm_c, in, out, prot);
+      case 16: return launch_tiles<ShallowTiles<16, BC>>(L, g, tm_in, tm_c, in, out, prot);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return launch_tiles<StreamTiles<8, CL>>(L, g, tm_in, tm_c, in, out, prot);
-    case 16: return launch_tiles<StreamTiles<16, CL>>(L, g, tm_in, tm_c, in, out, prot);
-    case 32: return launch_tiles<StreamTiles<32, CL>>(L, g, tm_in, tm_c, in, out, prot);
+    case 8: return launch_tiles<StreamTiles<8, BC>>(L, g, tm_in, tm_c, in, out, prot);
+    case 16: return launch_tiles<StreamTiles<16, BC>>(L, g, tm_in, tm_c, in, out, prot);
+    case 32: return launch_tiles<StreamTiles<32, BC>>(L, g, tm_in, tm_c, in, out, prot);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_sweep(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c, int in,
                          int out, bool prot) {
-  return g.bc == ABFT_BC_CLAMP ? launch_sweep_cl<true>(L, g, tm_in, tm_c, in, out, prot)
-                               : launch_sweep_cl<false>(L, g, tm_in, tm_c, in, out, prot);
+  switch (g.bc) {
+    case ABFT_BC_PERIODIC: return launch_sweep_bc<ABFT_BC_PERIODIC>(L, g, tm_in, tm_c, in, out, prot);
+    case ABFT_BC_ZERO: return launch_sweep_bc<ABFT_BC_ZERO>(L, g, tm_in, tm_c, in, out, prot);
+    default: return launch_sweep_bc<ABFT_BC_CLAMP>(L, g, tm_in, tm_c, in, out, prot);
+  }
 }
 
 template <class Tiles, int TY>
@@ -214,28 +217,31 @@ static cudaError_t redo_t(const Launch& L, const GridDev& g, const CUtensorMap& 
   return cudaGetLastError();
 }
 
-template <bool CL>
-static cudaError_t launch_redo_cl(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
+template <int BC>
+static cudaError_t launch_redo_bc(const Launch& L, const GridDev& g, const CUtensorMap& tm_in,
                                   const CUtensorMap& tm_c, int in, int out) {
   if (g.shallow) {
     switch (g.ty) {
-      case 8: return redo_t<ShallowTiles<8, CL>, 8>(L, g, tm_in, tm_c, in, out);
-      case 16: return redo_t<ShallowTiles<16, CL>, 16>(L, g, tm_in, tm_c, in, out);
+      case 8: return redo_t<ShallowTiles<8, BC>, 8>(L, g, tm_in, tm_c, in, out);
+      case 16: return redo_t<ShallowTiles<16, BC>, 16>(L, g, tm_in, tm_c, in, out);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.ty) {
-    case 8: return redo_t<StreamTiles<8, CL>, 8>(L, g, tm_in, tm_c, in, out);
-    case 16: return redo_t<StreamTiles<16, CL>, 16>(L, g, tm_in, tm_c, in, out);
-    case 32: return redo_t<StreamTiles<32, CL>, 32>(L, g, tm_in, tm_c, in, out);
+    case 8: return redo_t<StreamTiles<8, BC>, 8>(L, g, tm_in, tm_c, in, out);
+    case 16: return redo_t<StreamTiles<16, BC>, 16>(L, g, tm_in, tm_c, in, out);
+    case 32: return redo_t<StreamTiles<32, BC>, 32>(L, g, tm_in, tm_c, in, out);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_redo_tiles(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
                               int in, int out) {
-  return g.bc == ABFT_BC_CLAMP ? launch_redo_cl<true>(L, g, tm_in, tm_c, in, out)
-                               : launch_redo_cl<false>(L, g, tm_in, tm_c, in, out);
+  switch (g.bc) {
+    case ABFT_BC_PERIODIC: return launch_redo_bc<ABFT_BC_PERIODIC>(L, g, tm_in, tm_c, in, out);
+    case ABFT_BC_ZERO: return launch_redo_bc<ABFT_BC_ZERO>(L, g, tm_in, tm_c, in, out);
+    default: return launch_redo_bc<ABFT_BC_CLAMP>(L, g, tm_in, tm_c, in, out);
+  }
 }
 
 }  // namespace abft

@@ -318,13 +318,12 @@ __device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const 
 //   empty (zero): the in-plane zero fill is already right, the z faces become zero;
 //   periodic: the opposite face, read from the input grid in global memory (through
 //   L2: it was written by other CTAs in this launch or the previous one).
-// CLAMPED: compiled for the clamped rule alone (selects only); otherwise the rule is
-// read from g.bc.
-template <bool Z_STAGED, bool CLAMPED>
+// BC: the rule (abft_boundary), fixed at compile time.
+template <bool Z_STAGED, int BC>
 __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __restrict__ uin, int z, int y, int gx0,
                                                int last, const float4& c, float4& n, float4& s, float4& b, float4& t,
                                                float& w0, float& e0, float& e1, float& e2, float& e3) {
-  if (CLAMPED || g.bc == ABFT_BC_CLAMP) {
+  if (BC == ABFT_BC_CLAMP) {
     if (y == 0) n = c;
     if (y == g.ny - 1) s = c;
     if (gx0 == 0) w0 = c.x;
@@ -334,7 +333,7 @@ __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __
     if (last == 3) e3 = c.w;
     return;
   }
-  if (g.bc == ABFT_BC_ZERO) {
+  if (BC == ABFT_BC_ZERO) {
     if (z == 0) b = make_float4(0.f, 0.f, 0.f, 0.f);
     if (z == g.nz - 1) t = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
@@ -360,7 +359,7 @@ __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __
 
 // VEC: checksum vectors of the epilogue (2: a and b partials; 1: b partials only, for
 // the one-vector online check of Sec. 3.2)
-template <int TY, bool PROT, int ACC, bool CLAMPED, int VEC = 2>
+template <int TY, bool PROT, int ACC, int BC, int VEC = 2>
 __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
                                                const float* __restrict__ uin, float* __restrict__ uout, int txi, int tyi,
                                                DevCtrl* __restrict__ ctrl, const SweepSmem<TY>& sm, unsigned& seq,
@@ -421,7 +420,7 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       if (lane == 31) er = Uc[o + 4];
       float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      boundary_cells<false, CLAMPED>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
+      boundary_cells<false, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
@@ -666,7 +665,7 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
   tile_sync();
 }
 
-template <int TY, bool PROT, int ACC, bool CLAMPED, int VEC = 2>
+template <int TY, bool PROT, int ACC, int BC, int VEC = 2>
 __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* __restrict__ uin,
                                                  float* __restrict__ uout, int txi, int tyi,
                                                  DevCtrl* __restrict__ ctrl, const ShallowSmem<TY>& sm,
@@ -688,7 +687,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
   for (int z = warp; z < nz; z += NW) {
     const float* Uz = sm.u + z * PLANE;
     // at a z face: the centre plane, or for periodic boundaries the staged opposite face
-    const bool wrap = !CLAMPED && g.bc == ABFT_BC_PERIODIC;
+    constexpr bool wrap = BC == ABFT_BC_PERIODIC;
     const float* Ub = z > 0 ? Uz - PLANE : (wrap ? Uz + (nz - 1) * PLANE : Uz);
     const float* Ut = z + 1 < nz ? Uz + PLANE : (wrap ? sm.u : Uz);
     const float* Cz = sm.c + z * TY * kTX;
@@ -711,7 +710,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
       if (lane == 31) er = Uz[o + 4];
       float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      boundary_cells<true, CLAMPED>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
+      boundary_cells<true, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
@@ -786,10 +785,10 @@ __device__ void recompute_pa_shallow(const GridDev& g, const float* __restrict__
 // ---------------------------------------------------------------- tile policies
 // The persistent and per-launch kernels are written once against these.
 
-// CL: compiled for the clamped boundary alone (the default); false: the boundary rule
-// is read from GridDev::bc (periodic, empty).  The host picks the policy by the grid's
-// rule, so the clamped kernels carry no code for the others.
-template <int TY, bool CL = true>
+// BC: the boundary rule the tiles are compiled for (abft_boundary; clamped by default).
+// The host picks the policy by the grid's rule, so each kernel carries the code of its
+// rule only.
+template <int TY, int BC = ABFT_BC_CLAMP>
 struct StreamTiles {
   static constexpr int NW = SweepCfg<TY>::NW;
   SweepSmem<TY> sm;
@@ -807,7 +806,7 @@ struct StreamTiles {
   template <bool PROT, int ACC, int VEC = 2>
   __device__ __forceinline__ void run(const CUtensorMap* tm_u, const CUtensorMap* tm_c, const GridDev& g,
                                       const float* uin, float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
-    sweep_tile_run<TY, PROT, ACC, CL, VEC>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, sm, seq, pbuf);
+    sweep_tile_run<TY, PROT, ACC, BC, VEC>(tm_u, tm_c, g, uin, uout, txi, tyi, ctrl, sm, seq, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
@@ -815,7 +814,7 @@ struct StreamTiles {
   }
 };
 
-template <int TY, bool CL = true>
+template <int TY, int BC = ABFT_BC_CLAMP>
 struct ShallowTiles {
   static constexpr int NW = ShallowCfg<TY>::NW;
   ShallowSmem<TY> sm;
@@ -833,7 +832,7 @@ struct ShallowTiles {
   template <bool PROT, int ACC, int VEC = 2>
   __device__ __forceinline__ void run(const CUtensorMap*, const CUtensorMap*, const GridDev& g, const float* uin,
                                       float* uout, int txi, int tyi, DevCtrl* ctrl, int pbuf) {
-    shallow_tile_run<TY, PROT, ACC, CL, VEC>(g, uin, uout, txi, tyi, ctrl, sm, phase, pbuf);
+    shallow_tile_run<TY, PROT, ACC, BC, VEC>(g, uin, uout, txi, tyi, ctrl, sm, phase, pbuf);
   }
   template <int ACC>
   __device__ static void recompute_col(const GridDev& g, const float* u, void* PA, int tyi, int z, int x) {
