@@ -9,7 +9,8 @@
  *     boundaries (an out-of-range neighbour is the centre, Fig. 2), or periodic or
  *     empty (zero) ones (Sec. 3.3, "Dealing with Boundary Conditions");
  *   - per-plane row and column checksums a[z][x] = sum_y u, b[z][y] = sum_x u
- *     (Eq. 2, 3), fused into the sweep;
+ *     (Eq. 2, 3), fused into the sweep (both every sweep, or, as Sec. 3.2 recommends,
+ *     b every sweep and a only in planes where b failed: option `vectors`);
  *   - the interpolated checksums of Theorem 1 (Eq. 4, 5; boundary terms alpha, beta
  *     in closed form for each boundary rule; zero for the periodic one, which gives
  *     the simple form of Eq. 6, 7), the relative test of Sec. 3.4, location
