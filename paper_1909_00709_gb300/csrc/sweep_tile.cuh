@@ -318,11 +318,33 @@ __device__ __forceinline__ void sweep_tile_issue(const CUtensorMap* tm_u, const 
 //   empty (zero): the in-plane zero fill is already right, the z faces become zero;
 //   periodic: the opposite face, read from the input grid in global memory (through
 //   L2: it was written by other CTAs in this launch or the previous one).
+// Periodic boundaries: the opposite faces' values one row needs -- the wrapped x
+// neighbours of its first and last points and, on a y face, the row on the other face
+// -- loaded by wrap_row ahead of the row's computation (streaming tiles: one plane
+// ahead) so that the latency of these global loads is hidden; `pre` says they were.
+struct WrapRow {
+  float xw, xe;  // u at x = nx - 1 (for the point x = 0) and at x = 0 (for x = nx - 1)
+  float4 yf;     // the row on the other y face (rows y = 0 and y = ny - 1)
+};
+
+__device__ __forceinline__ WrapRow wrap_row(const GridDev& g, const float* __restrict__ uin, int z, int y, int gx0,
+                                            int last) {
+  WrapRow w{0.f, 0.f, make_float4(0.f, 0.f, 0.f, 0.f)};
+  if (y >= g.ny || last < 0) return w;
+  const float* row = uin + ((size_t)z * g.ny + y) * g.px;
+  if (gx0 == 0) w.xw = __ldcg(row + g.nx - 1);
+  if (last <= 3) w.xe = __ldcg(row);
+  if (y == 0) w.yf = __ldcg(reinterpret_cast<const float4*>(row + (size_t)(g.ny - 1) * g.px + gx0));
+  else if (y == g.ny - 1) w.yf = __ldcg(reinterpret_cast<const float4*>(row - (size_t)(g.ny - 1) * g.px + gx0));
+  return w;
+}
+
 // BC: the rule (abft_boundary), fixed at compile time.
 template <bool Z_STAGED, int BC>
 __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __restrict__ uin, int z, int y, int gx0,
                                                int last, const float4& c, float4& n, float4& s, float4& b, float4& t,
-                                               float& w0, float& e0, float& e1, float& e2, float& e3) {
+                                               float& w0, float& e0, float& e1, float& e2, float& e3,
+                                               const WrapRow* pre = nullptr) {
   if (BC == ABFT_BC_CLAMP) {
     if (y == 0) n = c;
     if (y == g.ny - 1) s = c;
@@ -341,16 +363,14 @@ __device__ __forceinline__ void boundary_cells(const GridDev& g, const float* __
   if (y >= g.ny || last < 0) return;  // no grid point among the four (gx0 < nx keeps the loads in the row)
   const size_t plane = (size_t)g.ny * g.px;
   const float* row = uin + (size_t)z * plane + (size_t)y * g.px;
-  if (y == 0) n = __ldcg(reinterpret_cast<const float4*>(row + (size_t)(g.ny - 1) * g.px + gx0));
-  if (y == g.ny - 1) s = __ldcg(reinterpret_cast<const float4*>(row - (size_t)(g.ny - 1) * g.px + gx0));
-  if (gx0 == 0) w0 = __ldcg(row + g.nx - 1);
-  if (last <= 3) {
-    const float e = __ldcg(row);
-    if (last == 0) e0 = e;
-    if (last == 1) e1 = e;
-    if (last == 2) e2 = e;
-    if (last == 3) e3 = e;
-  }
+  const WrapRow w = pre != nullptr ? *pre : wrap_row(g, uin, z, y, gx0, last);
+  if (y == 0) n = w.yf;
+  if (y == g.ny - 1) s = w.yf;  // for ny = 1 both wrap to the row itself
+  if (gx0 == 0) w0 = w.xw;
+  if (last == 0) e0 = w.xe;
+  if (last == 1) e1 = w.xe;
+  if (last == 2) e2 = w.xe;
+  if (last == 3) e3 = w.xe;
   if (!Z_STAGED) {
     if (z == 0) b = __ldcg(reinterpret_cast<const float4*>(row + (size_t)(g.nz - 1) * plane + gx0));
     if (z == g.nz - 1) t = __ldcg(reinterpret_cast<const float4*>(row - (size_t)(g.nz - 1) * plane + gx0));
@@ -390,8 +410,17 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
   constexpr bool SMEM_EPI = ACC == ABFT_ACC_FP32;
   constexpr bool PA_ON = PROT && VEC == 2;  // column partials (the a vector)
   static_assert(NW * kTX * 4 + TY * kRowPitch * 4 <= Cfg::RED_HALF, "FP32 epilogue buffer");
+  // periodic: the wrapped face values of this warp's rows, for this plane and the next
+  constexpr bool WRAP = BC == ABFT_BC_PERIODIC;
+  WrapRow wcur[WRAP ? Cfg::RPW : 1], wnxt[WRAP ? Cfg::RPW : 1];
+  if (WRAP)
+#pragma unroll
+    for (int rr = 0; rr < Cfg::RPW; ++rr) wcur[rr] = wrap_row(g, uin, 0, y0 + warp + rr * NW, gx0, last);
 
   for (int z = 0; z < nz; ++z) {
+    if (WRAP && z + 1 < nz)
+#pragma unroll
+      for (int rr = 0; rr < Cfg::RPW; ++rr) wnxt[rr] = wrap_row(g, uin, z + 1, y0 + warp + rr * NW, gx0, last);
     if (z == 0) wait(0);
     if (z + 1 < nz) wait(z + 1);
     const float* Uc = sm.stage_u((int)((base + z) % S));
@@ -420,7 +449,8 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       if (lane == 31) er = Uc[o + 4];
       float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      boundary_cells<false, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
+      boundary_cells<false, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3,
+                                WRAP ? &wcur[WRAP ? rr : 0] : nullptr);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
@@ -504,6 +534,9 @@ __device__ __forceinline__ void sweep_tile_run(const CUtensorMap* tm_u, const CU
       AccA<ACC>::template column_store<NW>(sm.red + (z & 1) * Cfg::RED_HALF, tid, PA,
                                            ((size_t)tyi * nz + z) * g.pa_stride + x0 + tid);
     }
+    if (WRAP)
+#pragma unroll
+      for (int rr = 0; rr < Cfg::RPW; ++rr) wcur[rr] = wnxt[rr];
   }
   seq = base + (unsigned)nz;
   fence_proxy_async_global();  // this thread's grid stores, before any later TMA read of them
