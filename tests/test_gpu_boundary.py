@@ -227,3 +227,26 @@ def test_periodic_checksums_follow_simple_form(abi, orc):
     u = ref["u"].reshape(shape[2], shape[1], shape[0])
     np.testing.assert_allclose(a.reshape(shape[2], shape[0]), u.sum(axis=1), rtol=1e-5)
     np.testing.assert_allclose(b.reshape(shape[2], shape[1]), u.sum(axis=2), rtol=1e-5)
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, ZERO])
+@pytest.mark.parametrize("path", ["per_launch", "persistent", "overlapped"])
+@pytest.mark.parametrize("shape", [(200, 37, 5), (300, 130, 6), (150, 40, 20)])
+def test_one_vector_face_flips_parity(abi, orc, shape, path, bc):
+    """One checksum vector per sweep (a summed on demand, with the rule's neighbours and
+    boundary terms) under periodic and empty boundaries: the oracle's events and values."""
+    steps = 20
+    flips = face_flips(shape, 3)
+    opt = {"per_launch": dict(persistent=0, overlap=0), "persistent": dict(persistent=1),
+           "overlapped": dict(persistent=0, overlap=1)}[path]
+    co = asym_coeffs(shape)
+    with context(abi, shape, 7, bc, coeffs=co, vectors=1, **opt) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(11, ONLINE)
+        ctx.step(steps - 11, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = oracle(orc, shape, 7, bc, steps, orc.MODE_ONLINE, flips, coeffs=co, vectors=1)
+    g, o = compare_events(ev, ref)
+    assert g == o and len(o) > 0
+    assert rel_err(got, ref["u"]) < tol(steps)
