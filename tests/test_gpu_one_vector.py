@@ -190,3 +190,22 @@ def test_full_size_512x512x8(abi, orc):
             ev = ctx.events()
         expect = {(int(f["step"]), int(f["z"]), int(f["y"]), int(f["x"]), 1) for f in sched if f["bit"] >= 16}
         assert {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"])) for e in ev} == expect
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("acc", [1, 2])
+def test_compensated_and_fp64_accumulation(abi, orc, acc, persistent):
+    """The TwoSum and FP64 variants with one vector (their kernels still form the column
+    partials, which the check ignores): the oracle's events and values."""
+    shape, steps = (200, 37, 5), 12
+    flips = inputs.flip_list([(3, 0, 2, 5, 7, 30), (5, 0, 0, 0, 0, 28), (8, 0, 4, 36, 199, 27),
+                              (8, 0, 1, 20, 150, 29), (8, 0, 1, 3, 10, 30)])
+    with gpu_context(abi, [shape], [2], vectors=1, acc=acc, persistent=persistent) as ctx:
+        ctx.inject_list(flips)
+        ctx.step(steps, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = oracle_run(orc, shape, 2, steps, orc.MODE_ONLINE, flips, vectors=1)
+    g, o = compare_events(ev, ref)
+    assert g == o and len(o) >= 4
+    assert rel_err(got, ref["u"]) < 1e-5
