@@ -422,3 +422,21 @@ def test_one_vector_detects_by_the_b_threshold(orc, bit):
     assert (both["n_events"] > 0) == (delta > ta)
     if ta < delta <= tb:  # seen by a alone: both vectors recompute its column
         assert [(int(e["y"]), int(e["x"]), int(e["kind"])) for e in both["events"]] == [(-1, x, orc.EV_RECOMPUTED)]
+
+
+@pytest.mark.parametrize("boundary", [PERIODIC, ZERO])
+def test_one_vector_square_grid_under_other_boundaries(orc, boundary):
+    """The one-vector rule under periodic and empty boundaries: on a square plane,
+    high-bit flips (faces included) give the events of testing both vectors."""
+    shape = (48, 48, 4)
+    co = inputs.hotspot_coeffs(*shape)
+    temp, power = inputs.grid_inputs(*shape, seed=9)
+    st = orc.Stencil(shape, orc.hotspot_points(co), boundary)
+    C = orc.source_term(power, co)
+    fl = inputs.flip_list([(2, 0, 0, 0, 0, 29), (4, 0, 3, 47, 47, 30), (6, 0, 1, 0, 20, 28), (8, 0, 2, 30, 0, 27)])
+    both = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl)
+    one = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, vectors=1)
+    key = lambda r: sorted((int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"]))
+                           for e in r["events"])
+    assert key(both) == key(one) and len(key(one)) == 4
+    assert all(k[4] == orc.EV_CORRECTED for k in key(one))
