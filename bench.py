@@ -6,11 +6,16 @@ Workload (default): one 512x512x8 FP32 HotSpot3D grid with synthetic inputs
 benchmark step with seeded bit flips at 1e-3 per sweep.  A benchmark step is one
 such 1000-sweep job (sweep, fused checksums, interpolation, detection, location,
 correction, injection).  Reported beside it: the unprotected sweep (overhead
-denominator) and the offline mode on the same grid, the dominant kernel's HBM
+denominator) and the offline mode on the same grid, the dominant kernel's
 roofline, the end-to-end job through the C ABI with host buffers, and the FP64
-CPU oracle on a bounded sample.
+CPU oracle (one whole job on all host cores, a sample on one core).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Roofline of the headline: the 24 MB working set of this grid stays in L2, so the
+dominant kernel's algorithmic bytes are set against the L2 copy bandwidth measured in
+the same run (abft_probe_l2_copy); the HBM roofline (measured copy bandwidth from
+MEASURED_PEAKS.json) is reported for the HBM-bound 1024x1024x256 grid.
 
 For N > 1 it is launched by torch.distributed.run; each rank runs an independent
 replica (the grid does not shard across GPUs), value = all ranks' updates / the
@@ -37,9 +42,10 @@ SWEEPS = 1000
 RATE = 1e-3
 BYTES_PER_UPDATE = 12  # read u, read C, write u' (neighbour reuse on chip)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-# DRAM bytes (read + write) of one 200-sweep launch of the dominant kernel, from one ncu
-# capture of this build (the working set stays in L2); None for kernels not captured
-TRAFFIC_PER_200_SWEEP_LAUNCH = {"k_persist_online": 16928768 + 96512}
+# DRAM bytes (read + write) per sweep of the dominant kernel, from one ncu capture of
+# the current build (the working set stays in L2); None for kernels not captured since
+# they last changed
+TRAFFIC_PER_SWEEP = {"k_persist_online": None}
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
@@ -56,13 +62,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-side", action="store_true", help="skip the precision study and the large grid")
+    p.add_argument("--no-cpu", action="store_true", help="skip every oracle run (CPU baseline, oracle comparisons)")
+    p.add_argument("--no-side", action="store_true", help="skip the side studies (precision, large grid, batch, ...)")
     p.add_argument("--profile", action="store_true",
                    help="short run for profilers: warm-up jobs, then one protected and one plain job")
     p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                    help="grid shape for --profile captures (default 512 512 8)")
     p.add_argument("--sweeps", type=int, default=None, help="sweeps per job for --profile captures")
+    p.add_argument("--mode", type=int, default=1, choices=[0, 1, 2],
+                   help="mode of the protected job of --profile captures (1 online, 2 offline)")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
                    help="abft_options field for --profile captures (e.g. tile_y=16)")
     p.add_argument("--vectors", type=int, default=1, choices=[1, 2],
@@ -76,6 +84,21 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def workload_config(vectors: int) -> dict:
+    """The benchmark step's workload; both arms print exactly this."""
+    return {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": SWEEPS, "mode": "online",
+            "flip_rate_per_sweep": RATE, "flip_seed": 1, "eps": 1e-5, "checksum_acc": "fp32-tile/fp64",
+            "checksum_vectors": vectors, "l2": "flushed (512 MiB write) before every timed step",
+            "parallelism": "replicas"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class Clocks:
@@ -124,19 +147,28 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def oracle_sample(sweeps: int, vectors: int = 1):
-    """The FP64 oracle on the same workload for `sweeps` online sweeps (single thread)."""
+# ------------------------------------------------------------------ oracle runs
+
+def oracle_job(shape, seed, sweeps, mode, flips=None, threads=None, **kw):
+    """One oracle run of a workload (FP64, OpenMP over z with `threads`); returns
+    (result dict, wall seconds)."""
     import oracle
     from paper_1909_00709_gb300 import inputs
     oracle.build()
-    co = inputs.hotspot_coeffs(*SHAPE)
-    temp, power = inputs.grid_inputs(*SHAPE, seed=1)
-    st = oracle.Stencil(SHAPE, oracle.hotspot_points(co))
+    oracle.set_threads(threads or host_cores())
+    co = inputs.hotspot_coeffs(*shape)
+    temp, power = inputs.grid_inputs(*shape, seed=seed)
+    st = oracle.Stencil(shape, oracle.hotspot_points(co))
     C = oracle.source_term(power, co)
-    sched = oracle.schedule(1, RATE, 0xFFFFFFFF, SHAPE, 0, sweeps)
     t0 = time.perf_counter()
-    oracle.run(st, C, temp, sweeps, oracle.MODE_ONLINE, sched, vectors=vectors)
-    return time.perf_counter() - t0
+    r = oracle.run(st, C, temp, sweeps, mode, flips, **kw)
+    return r, time.perf_counter() - t0
+
+
+def headline_schedule(sweeps):
+    import oracle
+    oracle.build()
+    return oracle.schedule(1, RATE, 0xFFFFFFFF, SHAPE, 0, sweeps)
 
 
 def n_points():
@@ -144,25 +176,196 @@ def n_points():
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: each step a bounded 20-sweep sample of the workload."""
+    """The oracle as the reference arm: every step is the benchmark step itself (the whole
+    1000-sweep online job of the headline workload, seeded flips), on all host cores."""
     if rank != 0:
         return
-    per = 20
+    import oracle
+    cores = host_cores()
+    sched = headline_schedule(SWEEPS)
     for _ in range(args.warmup):
-        oracle_sample(per, args.vectors)
-    ts = [oracle_sample(per, args.vectors) for _ in range(args.steps)]
+        oracle_job(SHAPE, 1, SWEEPS, oracle.MODE_ONLINE, sched, threads=cores, vectors=args.vectors)
+    ts = [oracle_job(SHAPE, 1, SWEEPS, oracle.MODE_ONLINE, sched, threads=cores, vectors=args.vectors)[1]
+          for _ in range(args.steps)]
     tot = sum(ts)
-    glups = n_points() * per * args.steps / tot / 1e9
+    glups = n_points() * SWEEPS * args.steps / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": per, "mode": "online",
-                       "flip_rate_per_sweep": RATE, "checksum_vectors": args.vectors},
-            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per} online sweeps of the {WORKLOAD} workload per step"},
+            "data": "synthetic", "config": workload_config(args.vectors),
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole {SWEEPS}-sweep online job of the {WORKLOAD} workload per step "
+                                       f"(OpenMP over z, {cores} threads)"},
             "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def ev_set(ev, grid=None):
+    return {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"])) for e in ev
+            if grid is None or "grid" not in ev.dtype.names or int(e["grid"]) == grid}
+
+
+def oracle_block(dev, stream, vectors):
+    """The FP64 oracle on every benchmark workload, single-threaded and on all host cores
+    (full length for 64x64x8, 512x512x8 and 512x512x64; labelled samples for the batch and
+    the 1024x1024x256 grid), with the GPU's located/corrected counts beside the oracle's.
+    Returns (block, 512x512x64 trajectory result)."""
+    import math
+    import oracle
+    from paper_1909_00709_gb300 import abi, inputs
+    cores = host_cores()
+    out = {"cores_all": cores, "note": "GLUP/s of the FP64 oracle; OpenMP over z (results identical for any "
+                                       "thread count)"}
+
+    def gpu_events(shapes, seeds, sweeps, mode, flips=None, seed=None, rate=None, **opt):
+        temps, powers, cos = [], [], []
+        for sh, sd in zip(shapes, seeds):
+            t, p = inputs.grid_inputs(*sh, seed=sd)
+            temps.append(t)
+            powers.append(p)
+            cos.append(inputs.hotspot_coeffs(*sh))
+        with abi.Context(shapes, temps, powers, cos, device=dev, stream=stream, **opt) as c:
+            if flips is not None:
+                c.inject_list(flips)
+            if seed is not None:
+                c.inject(seed, rate, 0xFFFFFFFF)
+            c.step(sweeps, mode)
+            return c.events(cap=1 << 20), c.counters()["rollbacks"]
+
+    def rate(shape, sweeps, secs):
+        return math.prod(shape) * sweeps / secs / 1e9
+
+    # 64x64x8: 100 online sweeps, one flip every 10 sweeps
+    sh0 = (64, 64, 8)
+    fl0 = inputs.flips_periodic(sh0, 100, 10, seed=0)
+    r0, t_all = oracle_job(sh0, 0, 100, oracle.MODE_ONLINE, fl0, threads=cores)
+    _, t_one = oracle_job(sh0, 0, 100, oracle.MODE_ONLINE, fl0, threads=1)
+    g0, _ = gpu_events([sh0], [0], 100, abi.MODE_ONLINE, flips=fl0)
+    out["hotspot3d_64x64x8"] = {"sweeps": 100, "length": "full", "glups_1": rate(sh0, 100, t_one),
+                                "glups_all": rate(sh0, 100, t_all), "oracle_events": len(r0["events"]),
+                                "gpu_events": len(g0), "events_identical": ev_set(g0) == ev_set(r0["events"])}
+    # 512x512x8: the benchmark step (1000 online sweeps, seeded flips at 1e-3 per sweep)
+    sched = headline_schedule(SWEEPS)
+    r1, t_all = oracle_job(SHAPE, 1, SWEEPS, oracle.MODE_ONLINE, sched, threads=cores, vectors=vectors)
+    _, t_one = oracle_job(SHAPE, 1, SWEEPS, oracle.MODE_ONLINE, sched, threads=1, vectors=vectors)
+    g1, _ = gpu_events([SHAPE], [1], SWEEPS, abi.MODE_ONLINE, seed=1, rate=RATE, vectors=vectors)
+    out[WORKLOAD] = {"sweeps": SWEEPS, "length": "full", "glups_1": rate(SHAPE, SWEEPS, t_one),
+                     "glups_all": rate(SHAPE, SWEEPS, t_all), "flips": len(sched),
+                     "oracle_events": len(r1["events"]), "gpu_events": len(g1),
+                     "events_identical": ev_set(g1) == ev_set(r1["events"])}
+    # 512x512x64: 500 fault-free online sweeps (also the precision study's trajectory)
+    r2, t_all = oracle_job(PRECISION_SHAPE, 2, PRECISION_SWEEPS, oracle.MODE_ONLINE, threads=cores)
+    n1 = 50
+    _, t_one = oracle_job(PRECISION_SHAPE, 2, n1, oracle.MODE_ONLINE, threads=1)
+    g2, _ = gpu_events([PRECISION_SHAPE], [2], PRECISION_SWEEPS, abi.MODE_ONLINE)
+    out["hotspot3d_512x512x64"] = {"sweeps": PRECISION_SWEEPS, "length": f"full on all cores; first {n1} sweeps "
+                                   "on one core", "glups_1": rate(PRECISION_SHAPE, n1, t_one),
+                                   "glups_all": rate(PRECISION_SHAPE, PRECISION_SWEEPS, t_all),
+                                   "oracle_events": len(r2["events"]), "gpu_events": len(g2)}
+    # the 256-grid batch: a sample of its first 8 grids, 10 online sweeps at 0.1 flips per
+    # sweep and grid (seeded, as a batch of 8); rate extrapolated per point-update
+    shapes = inputs.batch_shapes(BATCH_GRIDS, seed=3)[:8]
+    seeds = [1000 + i for i in range(8)]
+    ns = 10
+    ev3, _ = gpu_events(shapes, seeds, ns, abi.MODE_ONLINE, seed=9, rate=BATCH_RATE, batch=1)
+    t_all = t_one = 0.0
+    same, n_or = True, 0
+    for g, (sh, sd) in enumerate(zip(shapes, seeds)):
+        fl = oracle.schedule(9, BATCH_RATE, 0xFFFFFFFF, sh, 0, ns, grid=g, n_grids=len(shapes))
+        r, t = oracle_job(sh, sd, ns, oracle.MODE_ONLINE, fl, threads=cores)
+        t_all += t
+        t_one += oracle_job(sh, sd, 2, oracle.MODE_ONLINE, fl, threads=1)[1] * ns / 2
+        same &= ev_set(ev3, g) == ev_set(r["events"])
+        n_or += len(r["events"])
+    pts = sum(math.prod(sh) for sh in shapes)
+    out["hotspot3d_batch256"] = {"sweeps": ns, "length": f"sample: grids 0-7 of 256, {ns} sweeps on all cores, "
+                                 "2 sweeps on one core (scaled); extrapolated per point-update",
+                                 "glups_1": pts * ns / t_one / 1e9, "glups_all": pts * ns / t_all / 1e9,
+                                 "oracle_events": n_or, "gpu_events": len(ev3), "events_identical": same}
+    # 1024x1024x256: offline windows at the workload's flip rate; sample of one Delta = 2
+    # window (detected, rolled back and recomputed: 4 sweeps executed)
+    lam = 1e-6 * math.prod(LARGE_SHAPE)
+    fl4 = oracle.schedule(4, lam, 0xFFFFFFFF, LARGE_SHAPE, 0, 2)
+    r4, t_all = oracle_job(LARGE_SHAPE, 4, 2, oracle.MODE_OFFLINE, fl4, threads=cores, delta=2)
+    u4 = r4.pop("u")
+    del u4
+    _, t_one = oracle_job(LARGE_SHAPE, 4, 2, oracle.MODE_OFFLINE, fl4, threads=1, delta=2)
+    _, rb = gpu_events([LARGE_SHAPE], [4], 2, abi.MODE_OFFLINE, seed=4, rate=lam, delta=2, max_flips_per_step=511)
+    out["hotspot3d_1024x1024x256"] = {"sweeps": 2, "length": "sample: one offline window of 2 sweeps at 1e-6 "
+                                      "flips per point and sweep (rolled back: 4 sweeps executed); GLUP/s per "
+                                      "committed point-update, extrapolated",
+                                      "glups_1": rate(LARGE_SHAPE, 2, t_one), "glups_all": rate(LARGE_SHAPE, 2, t_all),
+                                      "flips": len(fl4), "oracle_rollbacks": r4["n_rollbacks"],
+                                      "gpu_rollbacks": rb}
+    return out, r2
+
+
+def precision_study(dev, stream, traj):
+    """512x512x64, 500 fault-free online sweeps per checksum accumulation: speed, the
+    largest passing residual, the grid and checksum error against the FP64 oracle's
+    trajectory (traj, None without the oracle), the accumulation error against exact sums
+    of the GPU's own grid, eps calibrated to 4x the residual, and the lowest bit whose
+    flips are all located at that eps (measured: 64 flips per bit, one per plane)."""
+    import numpy as np
+    import torch
+    from paper_1909_00709_gb300 import abi, inputs
+    shape = PRECISION_SHAPE
+    nx, ny, nz = shape
+    t, p = inputs.grid_inputs(*shape, seed=2)
+    co = inputs.hotspot_coeffs(*shape)
+    if traj is not None:
+        ou = traj["u"]
+        oa, ob = ou.sum(axis=1), ou.sum(axis=2)
+    prec = {}
+    for acc, name in enumerate(ACC_NAMES):
+        with abi.Context([shape], [t], [p], [co], device=dev, stream=stream, acc=acc) as c:
+            c.step(3, abi.MODE_ONLINE)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(PRECISION_SWEEPS, abi.MODE_ONLINE)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            glups = math_prod(shape) * PRECISION_SWEEPS / (e0.elapsed_time(e1) / 1e3) / 1e9
+        with abi.Context([shape], [t], [p], [co], device=dev, stream=stream, acc=acc, track_residual=1) as c:
+            c.step(PRECISION_SWEEPS, abi.MODE_ONLINE)
+            r = c.counters()["max_residual"]
+            n_ev = len(c.events())
+            u = c.read(0).astype(np.float64)
+            a, b = c.read_checksums(0)
+        a_ex, b_ex = u.sum(axis=1), u.sum(axis=2)  # FP64 sums of the GPU's FP32 grid
+        rel = lambda x, y: float(np.max(np.abs(x - y) / np.abs(y)))
+        d = {"glups": glups, "max_residual": r, "false_positives": n_ev,
+             "checksum_acc_err": max(rel(a, a_ex), rel(b, b_ex))}
+        if traj is not None:
+            d["err_vs_oracle"] = {"grid": rel(u, ou), "a": rel(a, oa), "b": rel(b, ob),
+                                  "oracle_max_residual": traj["max_resid"]}
+        eps = 4.0 * r
+        d["eps_calibrated"] = eps
+        # measured detection boundary at eps: 64 flips of bit k at sweep 3 + k, one per plane
+        rng = np.random.default_rng(55)
+        flips = [(3 + k, 0, z, int(rng.integers(ny)), int(rng.integers(nx)), k) for k in range(32)
+                 for z in range(nz)]
+        with abi.Context([shape], [t], [p], [co], device=dev, stream=stream, acc=acc, eps=eps,
+                         max_flips_per_step=nz) as c:
+            c.inject_list(inputs.flip_list(flips))
+            c.step(3 + 32 + 1, abi.MODE_ONLINE)
+            got = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"])): int(e["kind"]) for e in c.events()}
+        caught = {k: sum(1 for f in flips if f[5] == k and got.get((f[0], f[2], f[3], f[4])) == 1) for k in range(32)}
+        d["located_by_bit"] = caught
+        d["measured_bit"] = min(k for k in range(33) if all(caught.get(j, nz) == nz for j in range(k, 32)))
+        d["false_positives_at_eps"] = len(got) - sum(caught.values())
+        prec[name] = d
+    return {"shape": list(shape), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
+            "flips_per_bit": nz, "variants": prec,
+            "oracle": "FP64 oracle trajectory of the same 500 sweeps" if traj is not None else None}
+
+
+def math_prod(shape):
+    out = 1
+    for v in shape:
+        out *= int(v)
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -187,15 +390,22 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def timed_jobs(ctx, mode, k):
-        """k jobs of SWEEPS sweeps; L2 flushed before each; device time of the jobs only."""
+    def timed_jobs(ctx, mode, k, per_kernel=None):
+        """k jobs of SWEEPS sweeps; L2 flushed before each; device time of the jobs only.
+        With per_kernel (a dict), every kernel launch of the jobs is also bracketed by CUDA
+        events on the launching stream (abft_time_kernels) and summed there by kind."""
         total = 0.0
         for _ in range(k):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.step(SWEEPS, mode)
+            if per_kernel is None:
+                ctx.step(SWEEPS, mode)
+            else:
+                for kind, (ms, n) in ctx.time_kernels(SWEEPS, mode).items():
+                    a, b = per_kernel.get(kind, (0.0, 0))
+                    per_kernel[kind] = (a + ms, b + n)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             total += e0.elapsed_time(e1)
@@ -219,9 +429,10 @@ def run_ours(args, rank, world, local):
 
     clocks = Clocks(local)
     launches0 = prot.counters()["kernel_launches"]
+    kt = {}
     barrier()
     torch.cuda.synchronize(dev)
-    ms_prot = timed_jobs(prot, abi.MODE_ONLINE, args.steps)
+    ms_prot = timed_jobs(prot, abi.MODE_ONLINE, args.steps, per_kernel=kt)
     torch.cuda.synchronize(dev)
     barrier()
     launches = prot.counters()["kernel_launches"] - launches0
@@ -231,24 +442,35 @@ def run_ours(args, rank, world, local):
     ms_prot2 = timed_jobs(prot2, abi.MODE_ONLINE, args.steps)
     events = prot.events()
     off_cnt = off.counters()
-    side = side_runs(dev, stream, flush) if (rank == 0 and not args.no_side) else None
 
-    # dominant kernel: average launch duration from CUDA events on the launching stream.
-    # A persistent launch runs many sweeps; its algorithmic bytes are 12 B per point and sweep.
-    timed_sweeps = 200
-    kt = prot.time_kernels(timed_sweeps, abi.MODE_ONLINE)
+    # dominant kernel of the timed jobs: its average launch duration from the CUDA events
+    # that bracketed each of its launches inside the timed region
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_n = kt[dom]
-    sweeps_per_launch = timed_sweeps / dom_n if dom.startswith("persistent") else 1
+    sweeps_per_launch = SWEEPS * args.steps / dom_n if dom.startswith("persistent") else 1
     dom_avg_s = dom_ms / dom_n / 1e3
-    achieved = BYTES_PER_UPDATE * n_points() * sweeps_per_launch / dom_avg_s / 1e9
+    alg_bytes = BYTES_PER_UPDATE * n_points() * sweeps_per_launch
+    achieved = alg_bytes / dom_avg_s / 1e9
     kernel_names = {"persistent_protected": "k_persist_online", "sweep_protected": "k_sweep<protected>",
                     "check_online": "k_check_online"}
+    kname = kernel_names.get(dom, dom)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    traffic = TRAFFIC_PER_200_SWEEP_LAUNCH.get(kernel_names.get(dom, dom)) if timed_sweeps == 200 else None
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured (MEASURED_PEAKS.json, copy)" if "hbm_gbs" in peaks else "fallback"
+    # L2 copy bandwidth measured here: two buffers the size of one state buffer, best of 3
+    l2 = max(abi.probe_l2_copy(nb, 400, device=dev, stream=stream) for nb in (8 << 20, 12 << 20) for _ in range(3))
+    tps = TRAFFIC_PER_SWEEP.get(kname)
+    roofline = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                "traffic": tps * sweeps_per_launch if tps is not None else None, "kernel": kname,
+                "avg_launch_us": dom_avg_s * 1e6, "launches": dom_n, "sweeps_per_launch": sweeps_per_launch,
+                "us_per_sweep": dom_avg_s * 1e6 / sweeps_per_launch,
+                "peak_source": "measured in this run: abft_probe_l2_copy, 2 x 8-12 MiB L2-resident copy, best of 6",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "hbm_frac": achieved / hbm_peak, "hbm_peak": hbm_peak, "hbm_peak_source": hbm_src,
+                "note": "12 B per point-update x sweeps per launch / CUDA-event launch time inside the timed jobs; "
+                        "the 24 MB working set is L2-resident (ncu DRAM traffic ~0.3 % of the algorithmic bytes), "
+                        "so L2 bandwidth is the memory bound; hbm_frac is the same bytes over the HBM copy peak"}
 
     # end to end through the public API with host buffers: upload, 1000 sweeps, read back
     e2e = None
@@ -279,20 +501,23 @@ def run_ours(args, rank, world, local):
         return
     plain_glups = n_points() * SWEEPS * args.steps / (ms_plain / 1e3) / 1e9
     off_glups = n_points() * SWEEPS * args.steps / (ms_off / 1e3) / 1e9
-    cpu = None
+
+    cpu, orc_block, traj = None, None, None
     if not args.no_cpu and world == 1:
-        sweeps = 200
-        t = oracle_sample(sweeps, args.vectors)
-        cpu = {"value": n_points() * sweeps / t / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sweeps} online sweeps of the {WORKLOAD} workload (seeded flips, 1e-3/sweep)"}
+        orc_block, traj = oracle_block(dev, stream, args.vectors)
+        h = orc_block[WORKLOAD]
+        cpu = {"value": h["glups_all"], "unit": "GLUP/s", "cores": orc_block["cores_all"], "kind": "oracle",
+               "sample": f"the whole {SWEEPS}-sweep online job of the {WORKLOAD} workload (seeded flips, "
+                         f"1e-3/sweep), OpenMP over z on {orc_block['cores_all']} threads; the same job on 1 thread "
+                         f"beside it",
+               "cores_1": {"value": h["glups_1"], "cores": 1}, "cores_all": {"value": h["glups_all"],
+                                                                           "cores": orc_block["cores_all"]},
+               "events_identical": h["events_identical"]}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "shape": list(SHAPE), "sweeps_per_step": SWEEPS, "mode": "online",
-                   "flip_rate_per_sweep": RATE, "eps": 1e-5, "checksum_acc": "fp32-tile/fp64",
-                   "checksum_vectors": args.vectors,
-                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": "replicas"},
+        "config": workload_config(args.vectors),
         "overhead_pct": (ms_prot / ms_plain - 1.0) * 100.0,
         "unprotected_glups": plain_glups,
         f"online_{3 - args.vectors}_vectors": {
@@ -301,28 +526,26 @@ def run_ours(args, rank, world, local):
         "offline": {"glups": off_glups, "overhead_pct": (ms_off / ms_plain - 1.0) * 100.0, "delta": 16,
                     "rollbacks": off_cnt["rollbacks"]},
         "events": {"corrected": int((events["kind"] == 1).sum()), "recomputed": int((events["kind"] == 2).sum())},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),
-                     "avg_launch_us": dom_avg_s * 1e6, "sweeps_per_launch": sweeps_per_launch,
-                     "us_per_sweep": dom_avg_s * 1e6 / sweeps_per_launch, "peak_source": peak_src,
-                     "note": "algorithmic 12 B per point-update; the 24 MB working set is L2-resident"},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if side:
-        line.update(side)
-        line["large"]["roofline_frac"] = {k: v * BYTES_PER_UPDATE / peak for k, v in side["large"]["glups"].items()}
+    if orc_block is not None:
+        line["oracle"] = orc_block
+    if not args.no_side:
+        line["precision"] = precision_study(dev, stream, traj)
+        line.update(side_runs(dev, stream, flush, hbm_peak))
     print(json.dumps(line), flush=True)
     for c in (prot, prot2, plain, off):
         c.close()
 
 
-def side_runs(dev, stream, flush):
-    """The precision study (fault-free 512x512x64, three checksum accumulations), the
-    boundary rules, the large 1024x1024x256 grid (unprotected / online / offline), many
-    uneven grids, and the paper's campaigns, each timed with CUDA events."""
+def side_runs(dev, stream, flush, hbm_peak):
+    """The boundary rules, the large 1024x1024x256 grid (unprotected / online / offline,
+    autotuned, with its HBM roofline), many uneven grids, and the paper's campaigns, each
+    timed with CUDA events."""
     import math
     import numpy as np
     import torch
@@ -346,28 +569,6 @@ def side_runs(dev, stream, flush):
             n = shape[0] * shape[1] * shape[2]
             return n * sweeps / (ms / 1e3) / 1e9, c
 
-    prec = {}
-    shape = PRECISION_SHAPE
-    for acc, name in enumerate(ACC_NAMES):
-        glups, _ = timed(shape, abi.MODE_ONLINE, PRECISION_SWEEPS, 2, acc=acc)
-        t, p = inputs.grid_inputs(*shape, seed=2)
-        with abi.Context([shape], [t], [p], [inputs.hotspot_coeffs(*shape)], device=dev, stream=stream,
-                         acc=acc, track_residual=1) as c:
-            c.step(PRECISION_SWEEPS, abi.MODE_ONLINE)
-            r = c.counters()["max_residual"]
-            n_ev = len(c.events())
-            u = c.read(0).astype(np.float64)
-            a, b = c.read_checksums(0)
-        a_ex, b_ex = u.sum(axis=1), u.sum(axis=2)  # FP64 sums of the FP32 grid
-        err = max(float(np.max(np.abs(a - a_ex) / np.abs(a_ex))), float(np.max(np.abs(b - b_ex) / np.abs(b_ex))))
-        eps = 4.0 * r
-        # smallest mantissa bit whose flip moves every checksum it enters by more than the
-        # calibrated threshold plus the residual: |delta| = 2^(bit - 23 + e), e the value's binade
-        e_min = math.floor(math.log2(float(u.min())))
-        top = max(float(a_ex.max()), float(b_ex.max()))
-        bit = max(0, math.ceil(math.log2(1.25 * eps * top) - e_min + 23))
-        prec[name] = {"glups": glups, "max_residual": r, "false_positives": n_ev, "checksum_rel_err": err,
-                      "eps_calibrated": eps, "detectable_bit": bit}
     # boundary rules (Sec. 3.3): clamped, periodic and empty (zero) boundaries on the
     # L2-resident benchmark grid and on the HBM-bound 512x512x64 grid; offline where the
     # boundary terms vanish without the grid (clamped with the symmetric HotSpot weights,
@@ -395,12 +596,33 @@ def side_runs(dev, stream, flush):
         r["overhead_pct"] = {k: (r["unprotected"] / v - 1.0) * 100.0 for k, v in r.items() if k != "unprotected"}
         r["flips_per_sweep"] = rate
         onev["x".join(map(str, shape))] = r
-    large = {}
+    # the large grid: launch options autotuned per mode (tile rows, tile variant, persistent
+    # launches, temporal depth for the unprotected sweeps of unprotected runs and offline
+    # windows), then timed; the library defaults beside them
+    large, tuned_large = {}, {}
     lam = 1e-6 * math.prod(LARGE_SHAPE)  # flips per sweep
-    for name, mode, rate in (("unprotected", abi.MODE_NONE, 0.0), ("online", abi.MODE_ONLINE, 0.0),
-                             ("offline", abi.MODE_OFFLINE, 0.0), ("online_1_flip_per_sweep", abi.MODE_ONLINE, 1.0),
-                             ("online_flips", abi.MODE_ONLINE, lam), ("offline_flips", abi.MODE_OFFLINE, lam)):
-        large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511)
+    lt, lp = inputs.grid_inputs(*LARGE_SHAPE, seed=4)
+    ltd, lpd = torch.from_numpy(lt).to(dev), torch.from_numpy(lp).to(dev)
+    del lt, lp
+    lco = inputs.hotspot_coeffs(*LARGE_SHAPE)
+    t0 = time.perf_counter()
+    for mname, mode in (("unprotected", abi.MODE_NONE), ("online", abi.MODE_ONLINE), ("offline", abi.MODE_OFFLINE)):
+        tuned_large[mname], _ = abi.autotune([LARGE_SHAPE], [ltd], [lpd], [lco], mode, sweeps=10, device=dev,
+                                             stream=stream, max_flips_per_step=511)
+    tune_s = time.perf_counter() - t0
+    del ltd, lpd
+    for name, mode, rate, key, extra in (
+            ("unprotected", abi.MODE_NONE, 0.0, "unprotected", {}),
+            ("online", abi.MODE_ONLINE, 0.0, "online", {}),
+            ("online_1_vector", abi.MODE_ONLINE, 0.0, "online", {"vectors": 1}),
+            ("offline", abi.MODE_OFFLINE, 0.0, "offline", {}),
+            ("online_1_flip_per_sweep", abi.MODE_ONLINE, 1.0, "online", {}),
+            ("online_flips", abi.MODE_ONLINE, lam, "online", {}),
+            ("offline_flips", abi.MODE_OFFLINE, lam, "offline", {})):
+        large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, inject=rate, max_flips_per_step=511,
+                               **tuned_large[key], **extra)
+    for name, mode in (("unprotected_default_options", abi.MODE_NONE), ("offline_default_options", abi.MODE_OFFLINE)):
+        large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, max_flips_per_step=511)
     # many uneven grids: batched launches (one sweep launch per tile class, one check
     # launch per sweep, graphs of 50 sweeps, tiles autotuned; the unprotected run uses the
     # same options) against the same grids advanced one by one
@@ -498,12 +720,14 @@ def side_runs(dev, stream, flush):
     return {"boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16},
             "one_vector": {"glups": onev, "mode": "online; *_flips at the stated rate"}, "batch": batch,
             "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
-            "precision": {"shape": list(PRECISION_SHAPE), "sweeps": PRECISION_SWEEPS, "mode": "online, fault-free",
-                          "variants": prec},
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,
                       "flip_rate_per_sweep": "1e-6 per point in the *_flips runs", "glups": large,
+                      "tuned_options": tuned_large, "tuning_s": tune_s,
                       "overhead_pct": {k: (large["unprotected"] / v - 1.0) * 100.0
-                                       for k, v in large.items() if k != "unprotected"}}}
+                                       for k, v in large.items() if k != "unprotected"},
+                      "roofline_hbm": {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s",
+                                       "bytes_per_update": BYTES_PER_UPDATE,
+                                       "frac": {k: v * BYTES_PER_UPDATE / hbm_peak for k, v in large.items()}}}}
 
 
 def run_profile(args, local):
@@ -520,9 +744,9 @@ def run_profile(args, local):
     prot.inject(1, RATE, 0xFFFFFFFF)
     plain = abi.Context([SHAPE], [temp], [power], [co], **opts)
     for _ in range(args.warmup):
-        prot.step(SWEEPS, abi.MODE_ONLINE)
+        prot.step(SWEEPS, args.mode)
         plain.step(SWEEPS, abi.MODE_NONE)
-    prot.step(SWEEPS, abi.MODE_ONLINE)
+    prot.step(SWEEPS, args.mode)
     plain.step(SWEEPS, abi.MODE_NONE)
     torch.cuda.synchronize()
     print(json.dumps({"profile": WORKLOAD, "shape": list(SHAPE), "sweeps": SWEEPS,

@@ -241,6 +241,17 @@ ABFT_API abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out);
 #define ABFT_KERNEL_KINDS 8
 ABFT_API abft_status abft_time_kernels(abft_ctx* ctx, int64_t n, int32_t mode, double* ms, int64_t* launches);
 
+/* Measurement probe (no counterpart in the paper): the sustained L2 copy bandwidth that
+   bounds grids small enough to stay in L2.  Copies `bytes` (a multiple of 16) from src
+   to dst (device buffers, 16-byte aligned, not overlapping, both caller-owned) `passes`
+   (1..100000) times inside one launch of two CTAs per SM with 16-byte L2-only loads and
+   stores, after one untimed warm-up pass; *elapsed_ms receives the timed launch's CUDA-
+   event duration on `stream` (synchronised before return).  Bytes moved =
+   2 * bytes * passes.  Choose 2 * bytes well below the L2 size (e.g. 2 x 8 MiB).
+   Errors: ABFT_E_INVAL (arguments), ABFT_E_CUDA. */
+ABFT_API abft_status abft_probe_l2_copy(const void* src, void* dst, size_t bytes, int32_t passes, void* stream,
+                                        double* elapsed_ms);
+
 ABFT_API const char* abft_last_error(const abft_ctx* ctx);
 ABFT_API const char* abft_status_string(abft_status s);
 
@@ -285,6 +296,9 @@ ABFT_API abft_status abft_selftest_wait(int32_t which, int64_t limit_us, void* s
    The caller owns every buffer: u_in, C (constant term) and u_out are device FP32
    grids with rows of `pitch` elements (pitch >= nx, a multiple of 4; pointers
    16-byte aligned; u_out != u_in); a_out (nz*nx) and b_out (nz*ny) are device FP64.
+   The sweep uses the clamped boundary rule (Fig. 2) with the weights of *coeffs, and
+   the checksums are FP32 tile partials summed across tiles in FP64 (ABFT_ACC_FP32);
+   periodic or empty faces and the TwoSum/FP64 accumulations need a context.
    No context, workspace or allocation: the per-tile partial sums live in one fixed
    8 MiB device array inside the library, held by every GPU that loads it until
    the process exits.  Grids whose partials do not fit are refused.  The first call

@@ -65,8 +65,11 @@ def build(force: bool = False) -> str:
             return _LIB_PATH
         os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-Wall", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
+        try:  # OpenMP over the z loops when the toolchain has it
+            subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -76,6 +79,8 @@ def _load():
     if _lib is None:
         lib = ct.CDLL(build())
         P = ct.c_void_p
+        lib.orc_set_threads.argtypes = [ct.c_int32]
+        lib.orc_max_threads.restype = ct.c_int32
         lib.orc_source_term.argtypes = [ct.c_int64, P, ct.c_float, ct.c_float, ct.c_float, P]
         lib.orc_sweep.argtypes = [ct.POINTER(_Stencil), P, P, P]
         lib.orc_checksums.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, P, P, P]
@@ -94,6 +99,15 @@ def _load():
         lib.orc_schedule.restype = ct.c_int64
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's z loops (results do not depend on the count)."""
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
 
 
 def _ptr(a: np.ndarray):

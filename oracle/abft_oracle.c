@@ -37,6 +37,28 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads: the sweep, checksum and interpolation loops below split their outer z loop
+   (the sweep: its z and y loops) over OpenMP threads (one `parallel for`, nothing else).  Every output entry is still
+   computed by one thread in the same order, so results do not depend on the count. */
+void orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ helpers */
 
@@ -48,7 +70,8 @@ static int64_t lin(const orc_stencil* s, int64_t z, int64_t y, int64_t x) {
    ghost cell is an empty (zero) boundary cell. */
 static int map_axis(int64_t* i, int64_t n, int32_t boundary) {
   if (*i >= 0 && *i < n) return 1;
-  if (boundary == ORC_CLAMP) { /* Fig. 2: w = (x == 0) ? c : c - 1, per axis */
+  if (boundary == ORC_CLAMP) { /* Fig. 2: a neighbour outside the grid reads the nearest
+                                  in-range point on that axis */
     *i = *i < 0 ? 0 : n - 1;
     return 1;
   }
@@ -99,6 +122,7 @@ void orc_sweep(const orc_stencil* s, const double* C, const double* u, double* o
   const int r = stencil_radius(s);
   int64_t* off = malloc(sizeof(int64_t) * (s->npts > 0 ? s->npts : 1));
   for (int k = 0; k < s->npts; k++) off[k] = lin(s, s->pts[k].dz, s->pts[k].dy, s->pts[k].dx);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t z = 0; z < s->nz; z++)
     for (int64_t y = 0; y < s->ny; y++)
       for (int64_t x = 0; x < s->nx; x++) {
@@ -119,6 +143,7 @@ void orc_sweep(const orc_stencil* s, const double* C, const double* u, double* o
 /* ------------------------------------------------ Eq. (2), (3): checksums */
 
 void orc_checksums(int32_t nx, int32_t ny, int32_t nz, const double* u, double* a, double* b) {
+#pragma omp parallel for schedule(static)
   for (int64_t z = 0; z < nz; z++) {
     for (int64_t x = 0; x < nx; x++) {
       double t = 0.0;
@@ -181,6 +206,7 @@ static double beta(const orc_stencil* s, const double* u, int64_t z, int64_t y, 
 void orc_interpolate(const orc_stencil* s, const double* cx, const double* cy,
                      const double* a, const double* b, const double* u,
                      double* ap, double* bp) {
+#pragma omp parallel for schedule(static)
   for (int64_t z = 0; z < s->nz; z++) {
     for (int64_t x = 0; x < s->nx; x++) { /* Eq. (4) */
       double acc = 0.0;
@@ -210,6 +236,7 @@ static double vec_at(const double* v, int64_t n_line, int64_t nz, int32_t bounda
 
 void orc_interpolate_simple(const orc_stencil* s, const double* cx, const double* cy,
                             const double* a, const double* b, double* ap, double* bp) {
+#pragma omp parallel for schedule(static)
   for (int64_t z = 0; z < s->nz; z++) {
     for (int64_t x = 0; x < s->nx; x++) { /* Eq. (6) */
       double acc = 0.0;

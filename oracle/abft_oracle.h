@@ -56,6 +56,11 @@ typedef struct {
   int64_t n_flips_applied;
 } orc_out;
 
+/* OpenMP threads for the z loops of the sweep, checksums and interpolation (1 when the
+   library was built without OpenMP); results do not depend on the count */
+void orc_set_threads(int32_t n);
+int32_t orc_max_threads(void);
+
 /* HotSpot-like constant term of Eq. (1): C = sdc*P + c_amb*t_amb */
 void orc_source_term(int64_t n, const float* power, float sdc, float c_amb, float t_amb, double* C);
 

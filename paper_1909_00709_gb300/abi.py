@@ -28,7 +28,8 @@ EXPORTS = ("abft_default_options", "abft_workspace_bytes", "abft_init", "abft_st
            "abft_correct", "abft_inject", "abft_inject_list", "abft_schedule", "abft_events",
            "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
            "abft_last_error", "abft_status_string", "abft_destroy", "abft_sweep_checksums_static",
-           "abft_read_checksums", "abft_selftest_wait", "abft_tune_workspace_bytes", "abft_tune")
+           "abft_read_checksums", "abft_selftest_wait", "abft_tune_workspace_bytes", "abft_tune",
+           "abft_probe_l2_copy")
 
 
 class abft_grid(ct.Structure):
@@ -114,6 +115,7 @@ def lib(build_if_missing: bool = False):
     L.abft_tune.argtypes = [ct.POINTER(abft_grid), I32, ct.POINTER(P), ct.POINTER(P), ct.POINTER(abft_coeffs),
                             ct.POINTER(abft_options), I32, I32, P, ct.c_size_t, ct.POINTER(abft_options),
                             ct.POINTER(ct.c_double)]
+    L.abft_probe_l2_copy.argtypes = [P, P, ct.c_size_t, I32, P, ct.POINTER(ct.c_double)]
     L.abft_get_counters.argtypes = [P, ct.POINTER(abft_counters)]
     L.abft_time_kernels.argtypes = [P, I64, I32, P, P]
     L.abft_last_error.argtypes = [P]
@@ -124,7 +126,7 @@ def lib(build_if_missing: bool = False):
     L.abft_destroy.restype = None
     for name in ("abft_init", "abft_step", "abft_verify", "abft_correct", "abft_inject", "abft_inject_list",
                  "abft_events", "abft_read", "abft_current", "abft_get_counters", "abft_time_kernels",
-                 "abft_read_checksums", "abft_selftest_wait", "abft_tune"):
+                 "abft_read_checksums", "abft_selftest_wait", "abft_tune", "abft_probe_l2_copy"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -186,11 +188,28 @@ def abft_selftest_wait(which: int, limit_us: int, stream: int = 0):
     return st, ms.value
 
 
+def probe_l2_copy(nbytes: int = 8 << 20, passes: int = 400, *, device=None, stream=None) -> float:
+    """Sustained L2 copy bandwidth in GB/s (abft_probe_l2_copy on two torch-allocated
+    buffers of nbytes each; 2 * nbytes * passes bytes moved)."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    src = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+    dst = torch.empty_like(src)
+    ms = ct.c_double()
+    with torch.cuda.device(dev):
+        r = lib().abft_probe_l2_copy(ct.c_void_p(src.data_ptr()), ct.c_void_p(dst.data_ptr()), nbytes, passes,
+                                     ct.c_void_p(st.cuda_stream), ct.byref(ms))
+    if r != 0:
+        raise AbftError(r, "abft_probe_l2_copy failed")
+    return 2.0 * nbytes * passes / (ms.value / 1e3) / 1e9
+
+
 def abft_tune_workspace_bytes(shapes, opt: abft_options) -> int:
     return lib().abft_tune_workspace_bytes(_grids(shapes), len(shapes), ct.byref(opt))
 
 
-OPTION_KEYS = ("tile_y", "shallow", "persistent", "batch")
+OPTION_KEYS = ("tile_y", "shallow", "persistent", "batch", "depth")
 
 
 def autotune(shapes, temps, powers, coeffs, mode: int, sweeps: int = 20, *, device=None, stream=None, **opt_kw):

@@ -18,6 +18,10 @@
 //     streams, or two host threads) race on it; serialise them.
 //   - Grids whose partials exceed the array are refused with ABFT_E_INVAL.
 //   - Nothing here allocates: no cudaMalloc, cudaFree, pinned or managed memory.
+//   - The sweep applies the clamped boundary rule (Fig. 2) and forms FP32 tile
+//     partials that are reduced across tiles in FP64 (the ABFT_ACC_FP32 variant);
+//     callers that need periodic or empty faces, or TwoSum/FP64 accumulation, use a
+//     context.
 #include <cstring>
 #include <mutex>
 
@@ -36,7 +40,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_lock;
 void* g_scratch_ptr[kMaxDevices];  // device address of g_scratch, per device (null until set up)
 
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Once per device, with that device current: the device address of g_scratch.
 cudaError_t scratch_for_current_device(void** out) {
@@ -80,7 +84,8 @@ extern "C" ABFT_API abft_status abft_sweep_checksums_static(const float* u_in, c
   void* base = nullptr;
   if (scratch_for_current_device(&base) != cudaSuccess) return ABFT_E_CUDA;
   unsigned char* s = static_cast<unsigned char*>(base);
-  static_assert(sizeof(DevCtrl) + sizeof(DevGridCtrl) <= kCtrlBytes, "control block must fit");
+  // the grid control block sits at round_up(sizeof(DevCtrl), 16), as placed below
+  static_assert(round_up(sizeof(DevCtrl), 16) + sizeof(DevGridCtrl) <= kCtrlBytes, "control block must fit");
 
   GridDev g;
   memset(&g, 0, sizeof g);

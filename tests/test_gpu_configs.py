@@ -1,0 +1,221 @@
+"""Value and event parity with the FP64 oracle at the benchmark workloads' own sizes and
+lengths, in the launch configurations the benchmark times.
+
+  * 512x512x8, 1000 online sweeps with seeded flips at 1e-3 per sweep (one and two
+    checksum vectors), plus the fault-free run: the event set equals the oracle run's,
+    values within 1e-5 relative per 100 sweeps.
+  * 512x512x64, 500 fault-free online sweeps in each checksum accumulation: grid and
+    checksums against the oracle's trajectory, zero events on both sides.
+  * 1024x1024x256, one offline window of 16 sweeps and then 16 online sweeps at the
+    workload's flip rate (1e-6 per point and sweep, about 268 flips per sweep): equal
+    rollback counts and event sets, values against the oracle.
+  * four grids of the uneven 256-grid batch (shapes drawn from x, y in 64..1024 and
+    z in 4..64), advanced together by batched launches: events and values per grid.
+
+The oracle runs with OpenMP over its z loops (results do not depend on the thread
+count); each test prints the oracle's wall time."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_1909_00709_gb300 import inputs
+from _util import compare_events, gpu_context, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+ONLINE, OFFLINE, NONE = 1, 2, 0
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_00709_gb300 import abi, build
+    build.build()
+    abi.lib()
+    return abi
+
+
+def value_tol(steps):
+    return 1e-5 * max(1.0, steps / 100.0)
+
+
+def timed_oracle(orc, *a, **kw):
+    t0 = time.perf_counter()
+    r = oracle_run(orc, *a, **kw)
+    print(f"  oracle {a[0]} {a[2]} sweeps mode {a[3]}: {time.perf_counter() - t0:.1f} s "
+          f"on {orc.max_threads()} threads")
+    return r
+
+
+def marginal_mask(shape, marginal, last_step):
+    """Points whose value may differ because a (sweep, plane) pair fell inside the
+    oracle's guard band (detection there is decided by rounding): the plane and every
+    plane the stencil reaches from it by the end of the run."""
+    nx, ny, nz = shape
+    keep = np.ones((nz, ny, nx), dtype=bool)
+    for step, z in marginal:
+        reach = int(last_step - step)
+        keep[max(0, z - reach):min(nz, z + reach + 1)] = False
+    return keep
+
+
+# ---------------------------------------------------------------- 512x512x8, 1000 sweeps
+
+SHAPE1, STEPS1, RATE1 = (512, 512, 8), 1000, 1e-3
+
+
+@pytest.mark.parametrize("vectors", [1, 2])
+def test_512x512x8_1000_online_sweeps_fault_free(abi, orc, vectors):
+    with gpu_context(abi, [SHAPE1], [1], vectors=vectors) as ctx:
+        ctx.step(STEPS1, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = timed_oracle(orc, SHAPE1, 1, STEPS1, orc.MODE_ONLINE, vectors=vectors)
+    assert len(ev) == 0 and ref["n_events"] == 0
+    err = rel_err(got, ref["u"])
+    print(f"  max rel err after {STEPS1} sweeps: {err:.2e}")
+    assert err < value_tol(STEPS1)
+
+
+@pytest.mark.parametrize("vectors", [1, 2])
+@pytest.mark.parametrize("seed", [1, 2, 3, 5])
+def test_512x512x8_1000_online_sweeps_seeded_flips(abi, orc, seed, vectors):
+    """The benchmark's headline job (seed 1 is the benchmark's own): every event of the
+    GPU run equals the oracle run's, and the final grids agree."""
+    sched = orc.schedule(seed, RATE1, 0xFFFFFFFF, SHAPE1, 0, STEPS1)
+    with gpu_context(abi, [SHAPE1], [1], vectors=vectors) as ctx:
+        ctx.inject(seed, RATE1, 0xFFFFFFFF)
+        ctx.step(STEPS1, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+    ref = timed_oracle(orc, SHAPE1, 1, STEPS1, orc.MODE_ONLINE, sched, vectors=vectors)
+    g, o = compare_events(ev, ref)
+    print(f"  seed {seed}: {len(sched)} flips (bits {sorted(int(f['bit']) for f in sched)}), "
+          f"{len(o)} oracle events, marginal {sorted(ref['marginal'])}")
+    assert g == o
+    keep = marginal_mask(SHAPE1, ref["marginal"], STEPS1 - 1)
+    err = rel_err(got[keep], ref["u"][keep])
+    assert err < value_tol(STEPS1)
+
+
+def test_512x512x8_1000_offline_sweeps_seeded_flips(abi, orc):
+    """The offline job the benchmark times beside the headline (Delta = 16)."""
+    seed = 1
+    sched = orc.schedule(seed, RATE1, 0xFFFFFFFF, SHAPE1, 0, STEPS1)
+    with gpu_context(abi, [SHAPE1], [1]) as ctx:
+        ctx.inject(seed, RATE1, 0xFFFFFFFF)
+        ctx.step(STEPS1, OFFLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+        rb = ctx.counters()["rollbacks"]
+    ref = timed_oracle(orc, SHAPE1, 1, STEPS1, orc.MODE_OFFLINE, sched)
+    g, o = compare_events(ev, ref)
+    assert g == o
+    assert rb == ref["n_rollbacks"]
+    assert rel_err(got, ref["u"]) < value_tol(STEPS1)
+
+
+# -------------------------------------------------------------- 512x512x64, 500 sweeps
+
+SHAPE2, STEPS2 = (512, 512, 64), 500
+
+
+@pytest.fixture(scope="module")
+def trajectory2(orc):
+    ref = timed_oracle(orc, SHAPE2, 2, STEPS2, orc.MODE_ONLINE)
+    a, b = orc.checksums(ref["u"])
+    return ref, a, b
+
+
+@pytest.mark.parametrize("acc", [0, 1, 2])
+def test_512x512x64_500_sweeps_against_oracle_trajectory(abi, orc, trajectory2, acc):
+    """Each checksum accumulation (FP32 tile sums, TwoSum, FP64): zero events, the grid
+    and both checksum vectors against the oracle's 500-sweep trajectory."""
+    ref, oa, ob = trajectory2
+    with gpu_context(abi, [SHAPE2], [2], acc=acc) as ctx:
+        ctx.step(STEPS2, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+        a, b = ctx.read_checksums(0)
+    assert len(ev) == 0 and ref["n_events"] == 0
+    err = rel_err(got, ref["u"])
+    ea, eb = rel_err(a, oa), rel_err(b, ob)
+    print(f"  acc {acc}: grid {err:.2e}, a {ea:.2e}, b {eb:.2e} against the oracle")
+    assert err < value_tol(STEPS2)
+    assert ea < value_tol(STEPS2) and eb < value_tol(STEPS2)
+
+
+# ---------------------------------------------------------- 1024x1024x256, Delta + 16
+
+SHAPE4 = (1024, 1024, 256)
+
+
+def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc):
+    """One Delta = 16 offline window and 16 online sweeps at 1e-6 flips per point and
+    sweep: the window is rolled back and recomputed, then every online sweep locates
+    and corrects (or recomputes) what the oracle does."""
+    seed, delta = 4, 16
+    lam = 1e-6 * math.prod(SHAPE4)
+    s_off = orc.schedule(seed, lam, 0xFFFFFFFF, SHAPE4, 0, delta)
+    s_on = orc.schedule(seed, lam, 0xFFFFFFFF, SHAPE4, delta, 2 * delta)
+    with gpu_context(abi, [SHAPE4], [4], max_flips_per_step=511, delta=delta) as ctx:
+        ctx.inject(seed, lam, 0xFFFFFFFF)
+        ctx.step(delta, OFFLINE)
+        rb = ctx.counters()["rollbacks"]
+        mid = ctx.read(0)
+        ctx.step(delta, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events(cap=1 << 20)
+    co = inputs.hotspot_coeffs(*SHAPE4)
+    temp, power = inputs.grid_inputs(*SHAPE4, seed=4)
+    st = orc.Stencil(SHAPE4, orc.hotspot_points(co))
+    C = orc.source_term(power, co)
+    del power
+    t0 = time.perf_counter()
+    r_off = orc.run(st, C, temp, delta, orc.MODE_OFFLINE, s_off, delta=delta)
+    del temp
+    r_on = orc.run(st, C, r_off["u"], delta, orc.MODE_ONLINE, s_on, t0=delta, ev_cap=1 << 20)
+    print(f"  oracle 1024x1024x256 {2 * delta} sweeps (+{delta} recomputed): "
+          f"{time.perf_counter() - t0:.1f} s on {orc.max_threads()} threads")
+    assert rb == r_off["n_rollbacks"] == 1
+    assert rel_err(mid, r_off["u"]) < 1e-5
+    off_ev = {(int(e["step"]), int(e["kind"])) for e in ev if int(e["kind"]) == 3}
+    assert off_ev == {(int(e["step"]), int(e["kind"])) for e in r_off["events"]}
+    on_gpu = np.array([e for e in ev if int(e["kind"]) != 3], dtype=ev.dtype)
+    g, o = compare_events(on_gpu, r_on)
+    print(f"  {len(s_on)} online flips, {len(o)} oracle events, {len(r_on['marginal'])} marginal pairs")
+    assert len(o) > 100
+    assert g == o
+    keep = marginal_mask(SHAPE4, r_on["marginal"], 2 * delta - 1)
+    assert rel_err(got[keep], r_on["u"][keep]) < 1e-5
+
+
+# ------------------------------------------------------- four grids of the uneven batch
+
+BATCH_PICK = (2, 13, 7, 30)  # (899,623,6) (345,966,4) (439,917,35) (983,793,23)
+
+
+def test_batch_grids_from_workload_range(abi, orc):
+    shapes_all = inputs.batch_shapes(256, seed=3)
+    shapes = [shapes_all[i] for i in BATCH_PICK]
+    seeds = [1000 + i for i in BATCH_PICK]
+    steps, rate, seed = 100, 0.1, 9
+    with gpu_context(abi, shapes, seeds, batch=1) as ctx:
+        ctx.inject(seed, rate, 0xFFFFFFFF)
+        ctx.step(steps, ONLINE)
+        got = [ctx.read(g) for g in range(len(shapes))]
+        ev = ctx.events()
+    total = 0
+    for g, (sh, sd) in enumerate(zip(shapes, seeds)):
+        sched = orc.schedule(seed, rate, 0xFFFFFFFF, sh, 0, steps, grid=g, n_grids=len(shapes))
+        ref = timed_oracle(orc, sh, sd, steps, orc.MODE_ONLINE, sched)
+        gs, os_ = compare_events(ev, ref, grid=g)
+        assert gs == os_, (g, sh)
+        total += len(os_)
+        keep = marginal_mask(sh, ref["marginal"], steps - 1)
+        assert rel_err(got[g][keep], ref["u"][keep]) < value_tol(steps)
+    assert total > 0

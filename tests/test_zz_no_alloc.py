@@ -18,13 +18,14 @@ def pitched(torch, a, pitch):
     return t
 
 
-def test_static_entry_matches_context_path_on_two_calls():
+@pytest.mark.parametrize("shape,pitch", [((200, 37, 5), 224),   # two x-tiles, ragged in x and y
+                                         ((201, 37, 5), 204)])  # pitch a multiple of 4, not of 32
+def test_static_entry_matches_context_path_on_two_calls(shape, pitch):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1909_00709_gb300 import abi, build
     build.build()
-    shape = (200, 37, 5)  # two x-tiles, ragged in x and y
     nx, ny, nz = shape
     temp, power = inputs.grid_inputs(*shape, seed=21)
     co = inputs.hotspot_coeffs(*shape)
@@ -34,7 +35,6 @@ def test_static_entry_matches_context_path_on_two_calls():
         ctx.step(1, abi.MODE_NONE)
         ref2 = ctx.read(0).astype(np.float64)
 
-    pitch = 224
     f32 = np.float32
     C = (f32(co["sdc"]) * power.astype(f32) + f32(co["c_amb"]) * f32(co["t_amb"])).astype(f32)
     dC = pitched(torch, C, pitch)
@@ -45,16 +45,29 @@ def test_static_entry_matches_context_path_on_two_calls():
     b = torch.zeros((nz, ny), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
 
-    for src, dst, ref in ((u0, u1, ref1), (u1, u2, ref2)):
-        st = abi.abft_sweep_checksums_static(src.data_ptr(), dC.data_ptr(), dst.data_ptr(), a.data_ptr(),
-                                             b.data_ptr(), shape, pitch, co, stream)
-        assert st == 0, abi.abft_status_string(st)
+    # the FP64 oracle's two sweeps (Eq. 1) and checksums (Eq. 2, 3) of the same inputs
+    import oracle
+    st = oracle.Stencil(shape, oracle.hotspot_points(co))
+    Cd = oracle.source_term(power, co)
+    o1 = oracle.sweep(st, Cd, temp)
+    o2 = oracle.sweep(st, Cd, o1)
+
+    for src, dst, ref, orf in ((u0, u1, ref1, o1), (u1, u2, ref2, o2)):
+        st_ = abi.abft_sweep_checksums_static(src.data_ptr(), dC.data_ptr(), dst.data_ptr(), a.data_ptr(),
+                                              b.data_ptr(), shape, pitch, co, stream)
+        assert st_ == 0, abi.abft_status_string(st_)
         torch.cuda.synchronize()
         got = dst[:, :, :nx].cpu().numpy().astype(np.float64)
         assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-6
+        assert np.max(np.abs(got - orf) / np.abs(orf)) < 1e-6
+        # the padding columns past nx are never written
+        assert float(dst[:, :, nx:].abs().max().item() if pitch > nx else 0.0) == 0.0
         # the returned checksums are the row and column sums of the returned grid (Eq. 2, 3)
         np.testing.assert_allclose(a.cpu().numpy(), got.sum(axis=1), rtol=1e-6, atol=0)
         np.testing.assert_allclose(b.cpu().numpy(), got.sum(axis=2), rtol=1e-6, atol=0)
+        oa, ob = oracle.checksums(orf)
+        np.testing.assert_allclose(a.cpu().numpy(), oa, rtol=1e-6, atol=0)
+        np.testing.assert_allclose(b.cpu().numpy(), ob, rtol=1e-6, atol=0)
 
 
 def test_static_entry_refuses_grids_beyond_its_scratch():
