@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CLAMP, PERIODIC, ZERO = 0, 1, 2
+CLAMP, PERIODIC, ZERO, CONST = 0, 1, 2, 3
 MODE_NONE, MODE_ONLINE, MODE_OFFLINE = 0, 1, 2
 EV_CORRECTED, EV_RECOMPUTED, EV_ROLLBACK = 1, 2, 3
 TARGET_GRID, TARGET_A, TARGET_B = 0, 1, 2
@@ -41,7 +41,8 @@ class _Point(ct.Structure):
 
 class _Stencil(ct.Structure):
     _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
-                ("npts", ct.c_int32), ("pts", ct.POINTER(_Point)), ("boundary", ct.c_int32)]
+                ("npts", ct.c_int32), ("pts", ct.POINTER(_Point)), ("boundary", ct.c_int32),
+                ("bvalue", ct.c_double)]
 
 
 class _Opts(ct.Structure):
@@ -86,6 +87,7 @@ def _load():
         lib.orc_checksums.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, P, P, P]
         lib.orc_interpolate.argtypes = [ct.POINTER(_Stencil), P, P, P, P, P, P, P]
         lib.orc_interpolate_simple.argtypes = [ct.POINTER(_Stencil), P, P, P, P, P, P]
+        lib.orc_interpolate_chain.argtypes = [ct.POINTER(_Stencil), P, P, P, P, P, P, P]
         lib.orc_detect.argtypes = [ct.c_int64, P, P, ct.c_double, P]
         lib.orc_detect.restype = ct.c_int64
         lib.orc_run.argtypes = [ct.POINTER(_Stencil), P, P, ct.c_int64, ct.c_int64, ct.c_int32,
@@ -121,14 +123,15 @@ def hotspot_points(co: dict):
 
 
 class Stencil:
-    """Stencil set S on an nx*ny*nz grid with a boundary rule."""
+    """Stencil set S on an nx*ny*nz grid with a boundary rule (CONST: every cell outside
+    the grid holds `bvalue`)."""
 
-    def __init__(self, shape, points, boundary: int = CLAMP):
+    def __init__(self, shape, points, boundary: int = CLAMP, bvalue: float = 0.0):
         self.nx, self.ny, self.nz = (int(v) for v in shape)
         self.points = [(int(a), int(b), int(c), float(w)) for a, b, c, w in points]
         self._pts = (_Point * len(self.points))(*[_Point(*p) for p in self.points])
         self.c = _Stencil(self.nx, self.ny, self.nz, len(self.points),
-                          ct.cast(self._pts, ct.POINTER(_Point)), boundary)
+                          ct.cast(self._pts, ct.POINTER(_Point)), boundary, float(bvalue))
 
     @property
     def shape3(self):
@@ -180,6 +183,16 @@ def interpolate_simple(st: Stencil, cx, cy, a, b) -> tuple:
     ap, bp = np.empty_like(a), np.empty_like(b)
     _load().orc_interpolate_simple(ct.byref(st.c), _ptr(cx), _ptr(cy), _ptr(a), _ptr(b),
                                    _ptr(ap), _ptr(bp))
+    return ap, bp
+
+
+def interpolate_chain(st: Stencil, cx, cy, a, b, u) -> tuple:
+    """Theorem 1 on predicted vectors a, b with the boundary terms of state u."""
+    cx, cy, a, b = (_f64(v) for v in (cx, cy, a, b))
+    u = _f64(u, st.shape3)
+    ap, bp = np.empty_like(a), np.empty_like(b)
+    _load().orc_interpolate_chain(ct.byref(st.c), _ptr(cx), _ptr(cy), _ptr(a), _ptr(b), _ptr(u),
+                                  _ptr(ap), _ptr(bp))
     return ap, bp
 
 

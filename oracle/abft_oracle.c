@@ -30,7 +30,14 @@
  *  R7  Offline: checkpoint every Delta steps, chain Eq. (6)/(7) Delta times from the
  *      checkpoint's checksums, compare once at the window end, and on a mismatch
  *      restore the checkpoint and recompute the window without injection
- *      (Sec. 4.1, 4.2, Fig. 10).  Requires alpha = beta = 0 (checked).
+ *      (Sec. 4.1, 4.2, Fig. 10).  Where alpha, beta do not vanish (empty or constant
+ *      boundaries, clamped ones with unequal opposite weights or offsets beyond one)
+ *      each link of the chain is Theorem 1 with the terms alpha, beta of the state the
+ *      step starts from, taken from the window's own intermediate states (per-step
+ *      boundary terms; Theorem 1 defines them from u^t).
+ *  R13 Boundary rules (Sec. 3.3): clamped (Fig. 2: an outside neighbour reads the
+ *      nearest in-range point, per axis), periodic (the point on the opposite face),
+ *      empty (zero) and constant (every outside cell holds the value bvalue).
  */
 #include "abft_oracle.h"
 
@@ -79,14 +86,17 @@ static int map_axis(int64_t* i, int64_t n, int32_t boundary) {
     *i = ((*i % n) + n) % n;
     return 1;
   }
-  return 0; /* ORC_ZERO: "empty boundaries", Sec. 3.3 */
+  return 0; /* ORC_ZERO and ORC_CONST: an outside cell holds a fixed value, Sec. 3.3 */
 }
+
+/* the fixed value of a cell outside the grid (empty: 0, constant: bvalue) */
+static double outside(const orc_stencil* s) { return s->boundary == ORC_CONST ? s->bvalue : 0.0; }
 
 /* value of u at any coordinate, ghost cells included */
 static double ghost(const orc_stencil* s, const double* u, int64_t z, int64_t y, int64_t x) {
-  if (!map_axis(&z, s->nz, s->boundary)) return 0.0;
-  if (!map_axis(&y, s->ny, s->boundary)) return 0.0;
-  if (!map_axis(&x, s->nx, s->boundary)) return 0.0;
+  if (!map_axis(&z, s->nz, s->boundary)) return outside(s);
+  if (!map_axis(&y, s->ny, s->boundary)) return outside(s);
+  if (!map_axis(&x, s->nx, s->boundary)) return outside(s);
   return u[lin(s, z, y, x)];
 }
 
@@ -221,6 +231,41 @@ void orc_interpolate(const orc_stencil* s, const double* cx, const double* cy,
       for (int k = 0; k < s->npts; k++) {
         const orc_point* p = &s->pts[k];
         acc += p->w * (b_at(s, b, u, z + p->dz, y + p->dy) + beta(s, u, z + p->dz, y + p->dy, p->dx));
+      }
+      bp[z * s->ny + y] = cy[z * s->ny + y] + acc;
+    }
+  }
+}
+
+/* entry of a predicted vector v (n_line entries per plane; the collapsed axis has
+   n_coll cells) at a possibly outside (z, i): the boundary rule applied to the vector */
+static double chain_at(const orc_stencil* s, const double* v, int64_t n_line, int64_t n_coll, int64_t z,
+                       int64_t i) {
+  if (!map_axis(&z, s->nz, s->boundary) || !map_axis(&i, n_line, s->boundary))
+    return (double)n_coll * outside(s); /* a line of outside cells */
+  return v[z * n_line + i];
+}
+
+void orc_interpolate_chain(const orc_stencil* s, const double* cx, const double* cy,
+                           const double* a, const double* b, const double* u,
+                           double* ap, double* bp) {
+#pragma omp parallel for schedule(static)
+  for (int64_t z = 0; z < s->nz; z++) {
+    for (int64_t x = 0; x < s->nx; x++) { /* Eq. (4) */
+      double acc = 0.0;
+      for (int k = 0; k < s->npts; k++) {
+        const orc_point* p = &s->pts[k];
+        acc += p->w * (chain_at(s, a, s->nx, s->ny, z + p->dz, x + p->dx) +
+                       alpha(s, u, z + p->dz, x + p->dx, p->dy));
+      }
+      ap[z * s->nx + x] = cx[z * s->nx + x] + acc;
+    }
+    for (int64_t y = 0; y < s->ny; y++) { /* Eq. (5) */
+      double acc = 0.0;
+      for (int k = 0; k < s->npts; k++) {
+        const orc_point* p = &s->pts[k];
+        acc += p->w * (chain_at(s, b, s->ny, s->nx, z + p->dz, y + p->dy) +
+                       beta(s, u, z + p->dz, y + p->dy, p->dx));
       }
       bp[z * s->ny + y] = cy[z * s->ny + y] + acc;
     }
@@ -389,7 +434,7 @@ static void inject(const orc_stencil* s, const orc_flip* flips, int64_t nflips, 
 
 static int alpha_beta_vanish(const orc_stencil* s) {
   if (s->boundary == ORC_PERIODIC) return 1;
-  if (s->boundary == ORC_ZERO) return 0;
+  if (s->boundary == ORC_ZERO || s->boundary == ORC_CONST) return 0;
   /* clamped: every point (i, j, k) needs a partner (i, -j, k) and (-i, j, k) of equal weight,
      and in-plane offsets of at most one: for |j| = 2 the clamped terms of Theorem 1 are
      2 u_0 - u_{n-2} - u_{n-1} and 2 u_{n-1} - u_0 - u_1, whose sum does not vanish */
@@ -411,7 +456,8 @@ int orc_run(const orc_stencil* s, const double* C, double* u, int64_t t0, int64_
             int32_t mode, const orc_flip* flips, int64_t nflips, const orc_opts* o, orc_out* r) {
   const int64_t nx = s->nx, ny = s->ny, nz = s->nz;
   const int64_t n = nx * ny * nz;
-  if (mode == ORC_MODE_OFFLINE && (!alpha_beta_vanish(s) || o->delta < 1)) return -1;
+  if (mode == ORC_MODE_OFFLINE && o->delta < 1) return -1;
+  const int simple_chain = alpha_beta_vanish(s); /* Eq. (6)/(7) suffice (Fig. 10) */
 
   double* uq = malloc(sizeof(double) * n);
   double* ck = malloc(sizeof(double) * n);
@@ -463,16 +509,22 @@ int orc_run(const orc_stencil* s, const double* C, double* u, int64_t t0, int64_
       memcpy(Bck, B, sizeof(double) * nz * ny);
       int attempt = 0;
       for (;;) {
+        /* Fig. 10: interpolate Delta times from the checkpoint's checksums; with
+           per-step boundary terms each link reads the state its step starts from */
+        memcpy(Ap, Ack, sizeof(double) * nz * nx);
+        memcpy(Bp, Bck, sizeof(double) * nz * ny);
         for (int64_t k = 0; k < d; k++) {
+          if (!simple_chain) {
+            orc_interpolate_chain(s, cx, cy, Ap, Bp, u, An, Bn);
+            memcpy(Ap, An, sizeof(double) * nz * nx);
+            memcpy(Bp, Bn, sizeof(double) * nz * ny);
+          }
           orc_sweep(s, C, u, uq);
           if (attempt == 0) inject(s, flips, nflips, t + k, ORC_TARGET_GRID, uq, A, B, r);
           memcpy(u, uq, sizeof(double) * n);
         }
         orc_checksums(s->nx, s->ny, s->nz, u, A, B);
-        /* Fig. 10: interpolate Delta times from the checkpoint's checksums */
-        memcpy(Ap, Ack, sizeof(double) * nz * nx);
-        memcpy(Bp, Bck, sizeof(double) * nz * ny);
-        for (int64_t k = 0; k < d; k++) {
+        for (int64_t k = 0; simple_chain && k < d; k++) {
           orc_interpolate_simple(s, cx, cy, Ap, Bp, An, Bn);
           memcpy(Ap, An, sizeof(double) * nz * nx);
           memcpy(Bp, Bn, sizeof(double) * nz * ny);

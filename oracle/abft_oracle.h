@@ -18,7 +18,7 @@
 extern "C" {
 #endif
 
-enum { ORC_CLAMP = 0, ORC_PERIODIC = 1, ORC_ZERO = 2 };
+enum { ORC_CLAMP = 0, ORC_PERIODIC = 1, ORC_ZERO = 2, ORC_CONST = 3 };
 enum { ORC_MODE_NONE = 0, ORC_MODE_ONLINE = 1, ORC_MODE_OFFLINE = 2 };
 enum { ORC_EV_CORRECTED = 1, ORC_EV_RECOMPUTED = 2, ORC_EV_ROLLBACK = 3 };
 enum { ORC_TARGET_GRID = 0, ORC_TARGET_A = 1, ORC_TARGET_B = 2 };
@@ -30,7 +30,8 @@ typedef struct {
   int32_t nx, ny, nz;
   int32_t npts;
   const orc_point* pts;
-  int32_t boundary; /* ORC_CLAMP (Fig. 2), ORC_PERIODIC, ORC_ZERO */
+  int32_t boundary; /* ORC_CLAMP (Fig. 2), ORC_PERIODIC, ORC_ZERO, ORC_CONST */
+  double bvalue;    /* ORC_CONST: the value every cell outside the grid holds */
 } orc_stencil;
 
 /* a bit-flip: at step `step`, XOR bit `bit` of the FP32 image of the target value */
@@ -74,6 +75,15 @@ void orc_checksums(int32_t nx, int32_t ny, int32_t nz, const double* u, double* 
 void orc_interpolate(const orc_stencil* s, const double* cx, const double* cy,
                      const double* a, const double* b, const double* u,
                      double* ap, double* bp);
+
+/* Theorem 1 (Eq. 4, 5) for a chain of predictions: a, b are predicted vectors (not sums of
+   u); every vector entry outside the grid is the rule applied to the vector (clamped or
+   wrapped index, 0 for empty boundaries, n*K for constant ones with n the collapsed
+   axis' length), and alpha, beta are evaluated literally from the state u the step
+   starts from (per-step boundary terms) */
+void orc_interpolate_chain(const orc_stencil* s, const double* cx, const double* cy,
+                           const double* a, const double* b, const double* u,
+                           double* ap, double* bp);
 
 /* Eq. (6), (7): Theorem 1 with alpha = beta = 0 (the boundary rule applied to the vectors) */
 void orc_interpolate_simple(const orc_stencil* s, const double* cx, const double* cy,

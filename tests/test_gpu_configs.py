@@ -82,10 +82,12 @@ def test_512x512x8_1000_online_sweeps_fault_free(abi, orc, vectors):
 
 
 @pytest.mark.parametrize("vectors", [1, 2])
-@pytest.mark.parametrize("seed", [1, 2, 3, 5])
+@pytest.mark.parametrize("seed", [1, 5, 24, 56])
 def test_512x512x8_1000_online_sweeps_seeded_flips(abi, orc, seed, vectors):
-    """The benchmark's headline job (seed 1 is the benchmark's own): every event of the
-    GPU run equals the oracle run's, and the final grids agree."""
+    """The benchmark's headline job: seed 1 is the benchmark's own (no flip lands in its
+    1000 sweeps at 1e-3 per sweep); seeds 5, 24 and 56 draw two to four flips each, bits
+    from 3 to 31, so detected and undetected flips both occur.  Every event of the GPU
+    run equals the oracle run's, and the final grids agree."""
     sched = orc.schedule(seed, RATE1, 0xFFFFFFFF, SHAPE1, 0, STEPS1)
     with gpu_context(abi, [SHAPE1], [1], vectors=vectors) as ctx:
         ctx.inject(seed, RATE1, 0xFFFFFFFF)
@@ -154,33 +156,54 @@ def test_512x512x64_500_sweeps_against_oracle_trajectory(abi, orc, trajectory2, 
 SHAPE4 = (1024, 1024, 256)
 
 
-def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc):
-    """One Delta = 16 offline window and 16 online sweeps at 1e-6 flips per point and
-    sweep: the window is rolled back and recomputed, then every online sweep locates
-    and corrects (or recomputes) what the oracle does."""
-    seed, delta = 4, 16
+SEED4, DELTA4 = 4, 16
+
+
+@pytest.fixture(scope="module")
+def oracle4(orc):
+    """The oracle's Delta = 16 offline window and 16 online sweeps at 1e-6 flips per point."""
     lam = 1e-6 * math.prod(SHAPE4)
-    s_off = orc.schedule(seed, lam, 0xFFFFFFFF, SHAPE4, 0, delta)
-    s_on = orc.schedule(seed, lam, 0xFFFFFFFF, SHAPE4, delta, 2 * delta)
-    with gpu_context(abi, [SHAPE4], [4], max_flips_per_step=511, delta=delta) as ctx:
-        ctx.inject(seed, lam, 0xFFFFFFFF)
-        ctx.step(delta, OFFLINE)
-        rb = ctx.counters()["rollbacks"]
-        mid = ctx.read(0)
-        ctx.step(delta, ONLINE)
-        got = ctx.read(0)
-        ev = ctx.events(cap=1 << 20)
+    s_off = orc.schedule(SEED4, lam, 0xFFFFFFFF, SHAPE4, 0, DELTA4)
+    s_on = orc.schedule(SEED4, lam, 0xFFFFFFFF, SHAPE4, DELTA4, 2 * DELTA4)
     co = inputs.hotspot_coeffs(*SHAPE4)
-    temp, power = inputs.grid_inputs(*SHAPE4, seed=4)
+    temp, power = inputs.grid_inputs(*SHAPE4, seed=SEED4)
     st = orc.Stencil(SHAPE4, orc.hotspot_points(co))
     C = orc.source_term(power, co)
     del power
     t0 = time.perf_counter()
-    r_off = orc.run(st, C, temp, delta, orc.MODE_OFFLINE, s_off, delta=delta)
+    r_off = orc.run(st, C, temp, DELTA4, orc.MODE_OFFLINE, s_off, delta=DELTA4)
     del temp
-    r_on = orc.run(st, C, r_off["u"], delta, orc.MODE_ONLINE, s_on, t0=delta, ev_cap=1 << 20)
-    print(f"  oracle 1024x1024x256 {2 * delta} sweeps (+{delta} recomputed): "
+    r_on = orc.run(st, C, r_off["u"], DELTA4, orc.MODE_ONLINE, s_on, t0=DELTA4, ev_cap=1 << 20)
+    print(f"  oracle 1024x1024x256 {2 * DELTA4} sweeps (+{DELTA4} recomputed): "
           f"{time.perf_counter() - t0:.1f} s on {orc.max_threads()} threads")
+    return lam, s_on, r_off, r_on
+
+
+@pytest.mark.parametrize("acc,tol", [(1, 1e-5), (0, 1e-4)])
+def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc, oracle4, acc, tol):
+    """One Delta = 16 offline window and 16 online sweeps at 1e-6 flips per point and
+    sweep: the window is rolled back and recomputed, then every online sweep locates
+    and corrects (or recomputes) what the oracle does.
+
+    Values: the window (rolled back, recomputed without flips) within 1e-5.  After the
+    online sweeps, a point written by Eq. (8) carries the rounding error of the
+    interpolated checksum it was computed from, while the oracle's checksums are exact.
+    With compensated (TwoSum) tile sums that error is the FP32 sweep's own rounding summed
+    along a line (about sqrt(n) half-ulps of the line's 1024 values, a few 1e-4 K on
+    330 K), so the whole grid holds 1e-5.  With plain FP32 tile sums the partial sums'
+    own rounding (about sqrt(n) ulps of a 16-row partial, ~1e-2 K) enters each corrected
+    value: bound 1e-4 relative (the paper's own accuracy study reports a median l2 error
+    below 1e-4 after a corrected flip, Sec. 5.2)."""
+    lam, s_on, r_off, r_on = oracle4
+    with gpu_context(abi, [SHAPE4], [SEED4], max_flips_per_step=511, delta=DELTA4, acc=acc,
+                     event_capacity=1 << 16) as ctx:
+        ctx.inject(SEED4, lam, 0xFFFFFFFF)
+        ctx.step(DELTA4, OFFLINE)
+        rb = ctx.counters()["rollbacks"]
+        mid = ctx.read(0)
+        ctx.step(DELTA4, ONLINE)
+        got = ctx.read(0)
+        ev = ctx.events(cap=1 << 20)
     assert rb == r_off["n_rollbacks"] == 1
     assert rel_err(mid, r_off["u"]) < 1e-5
     off_ev = {(int(e["step"]), int(e["kind"])) for e in ev if int(e["kind"]) == 3}
@@ -190,8 +213,10 @@ def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc):
     print(f"  {len(s_on)} online flips, {len(o)} oracle events, {len(r_on['marginal'])} marginal pairs")
     assert len(o) > 100
     assert g == o
-    keep = marginal_mask(SHAPE4, r_on["marginal"], 2 * delta - 1)
-    assert rel_err(got[keep], r_on["u"][keep]) < 1e-5
+    keep = marginal_mask(SHAPE4, r_on["marginal"], 2 * DELTA4 - 1)
+    err = rel_err(got[keep], r_on["u"][keep])
+    print(f"  acc {acc}: max rel err {err:.2e} (bound {tol:.0e})")
+    assert err < tol
 
 
 # ------------------------------------------------------- four grids of the uneven batch
@@ -209,13 +234,17 @@ def test_batch_grids_from_workload_range(abi, orc):
         ctx.step(steps, ONLINE)
         got = [ctx.read(g) for g in range(len(shapes))]
         ev = ctx.events()
-    total = 0
+    total, compared = 0, 0
     for g, (sh, sd) in enumerate(zip(shapes, seeds)):
         sched = orc.schedule(seed, rate, 0xFFFFFFFF, sh, 0, steps, grid=g, n_grids=len(shapes))
         ref = timed_oracle(orc, sh, sd, steps, orc.MODE_ONLINE, sched)
         gs, os_ = compare_events(ev, ref, grid=g)
+        print(f"  grid {sh}: {len(sched)} flips, {len(os_)} events, marginal {sorted(ref['marginal'])}")
         assert gs == os_, (g, sh)
         total += len(os_)
+        # planes a marginal (guard-band) flip may have reached are left out of the values
         keep = marginal_mask(sh, ref["marginal"], steps - 1)
-        assert rel_err(got[g][keep], ref["u"][keep]) < value_tol(steps)
-    assert total > 0
+        if keep.any():
+            assert rel_err(got[g][keep], ref["u"][keep]) < value_tol(steps)
+            compared += 1
+    assert total > 0 and compared >= 3

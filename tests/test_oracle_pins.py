@@ -9,7 +9,7 @@ import pytest
 
 from paper_1909_00709_gb300 import inputs
 
-CLAMP, PERIODIC, ZERO = 0, 1, 2
+CLAMP, PERIODIC, ZERO, CONST = 0, 1, 2, 3
 
 
 def seven(cc, cw, ce, cn, cs, cb, ct):
@@ -325,17 +325,57 @@ def test_offline_matches_unprotected_when_fault_free(orc):
     assert a["n_events"] == 0
 
 
-def test_offline_refuses_nonvanishing_boundary_terms(orc):
-    st = orc.Stencil((8, 8, 2), ASYM, CLAMP)
-    u = int_grid((8, 8, 2), 1)
-    with pytest.raises(RuntimeError):
-        orc.run(st, np.zeros_like(u), u, 4, orc.MODE_OFFLINE, delta=2)
+def dyadic_asym():
+    """Clamped-stable weights with every opposite pair unequal, summing to 1, dyadic."""
+    return seven(1 / 2, 1 / 16, 1 / 8, 1 / 32, 3 / 32, 1 / 16, 1 / 8)
+
+
+@pytest.mark.parametrize("rule,bval", [(CLAMP, 0.0), (ZERO, 0.0), (CONST, 300.0)],
+                         ids=["clamp-asym", "zero", "const"])
+def test_offline_per_step_terms_fault_free(orc, rule, bval):
+    """Where the terms of Theorem 1 do not vanish, the chain of Fig. 10 takes them from
+    each step's own state: a fault-free offline run has no event and equals the
+    unprotected run bit for bit."""
+    shape = (20, 18, 5)
+    co = inputs.hotspot_coeffs(*shape)
+    _, power = inputs.grid_inputs(*shape, seed=6)
+    temp, _ = inputs.grid_inputs(*shape, seed=7)
+    C = orc.source_term(power, co)
+    st = orc.Stencil(shape, dyadic_asym() if rule == CLAMP else orc.hotspot_points(co), rule, bval)
+    a = orc.run(st, C, temp, 37, orc.MODE_OFFLINE, delta=8)
+    b = orc.run(st, C, temp, 37, orc.MODE_NONE)
+    assert a["n_events"] == 0 and a["n_rollbacks"] == 0
+    np.testing.assert_array_equal(a["u"], b["u"])
+    assert a["max_resid"] < 1e-12
+
+
+@pytest.mark.parametrize("rule,bval", [(CLAMP, 0.0), (ZERO, 0.0), (CONST, 300.0)],
+                         ids=["clamp-asym", "zero", "const"])
+@pytest.mark.parametrize("where", ["y0", "ylast", "x0", "corner", "inner"])
+def test_offline_per_step_terms_catch_edge_flips(orc, rule, bval, where):
+    """A flip on a face row, which also enters the per-step boundary terms of the chain,
+    is still detected at the window's end; the rollback restores the fault-free run."""
+    shape = (20, 18, 5)
+    co = inputs.hotspot_coeffs(*shape)
+    _, power = inputs.grid_inputs(*shape, seed=6)
+    temp, _ = inputs.grid_inputs(*shape, seed=7)
+    C = orc.source_term(power, co)
+    st = orc.Stencil(shape, dyadic_asym() if rule == CLAMP else orc.hotspot_points(co), rule, bval)
+    zyx = dict(y0=(2, 0, 7), ylast=(2, 17, 7), x0=(3, 9, 0), corner=(0, 0, 19), inner=(2, 9, 9))[where]
+    for step in (9, 13, 15):  # early, middle and last sweep of the window 8..15
+        fl = inputs.flip_list([(step, 0, *zyx, 27)])
+        r = orc.run(st, C, temp, 24, orc.MODE_OFFLINE, fl, delta=8)
+        ref = orc.run(st, C, temp, 24, orc.MODE_OFFLINE, delta=8)
+        assert r["n_rollbacks"] == 1, (step, zyx)
+        assert [int(e["step"]) for e in r["events"]] == [8]
+        np.testing.assert_array_equal(r["u"], ref["u"])
 
 
 def test_clamped_radius_two_terms_do_not_vanish(orc):
     """A symmetric 13-point star under clamped boundaries: the simple form of Eq. (6)/(7)
     misses the terms of Theorem 1 (exact integer arithmetic shows the gap), so the
-    offline chain, which needs them to vanish, is refused; periodic boundaries accept it."""
+    offline chain takes the terms from each step's state (per step); periodic boundaries
+    need none."""
     pts = [(0, 0, 0, 4.0)] + [(d * s, 0, 0, 1.0) for d in (1, 2) for s in (-1, 1)] + \
           [(0, d * s, 0, 1.0) for d in (1, 2) for s in (-1, 1)] + [(0, 0, s, 1.0) for s in (-1, 1)]
     shape = (9, 7, 3)
@@ -350,10 +390,90 @@ def test_clamped_radius_two_terms_do_not_vanish(orc):
     ap, bp = orc.interpolate(st, *orc.checksums(C), a0, b0, u)
     np.testing.assert_array_equal(ap, a_true)
     np.testing.assert_array_equal(bp, b_true)
-    with pytest.raises(RuntimeError):
-        orc.run(st, C, u, 4, orc.MODE_OFFLINE, delta=2)
+    ap, bp = orc.interpolate_chain(st, *orc.checksums(C), a0, b0, u)
+    np.testing.assert_array_equal(ap, a_true)
+    np.testing.assert_array_equal(bp, b_true)
+    assert orc.run(st, C, u, 4, orc.MODE_OFFLINE, delta=2)["n_events"] == 0
     per = orc.Stencil(shape, pts, PERIODIC)
     assert orc.run(per, C, u, 4, orc.MODE_OFFLINE, delta=2)["n_events"] == 0
+
+
+# ----------------------------------------- general stencil sets and the constant rule
+
+STAR13 = [(0, 0, 0, 4.0)] + [(d * s, 0, 0, float(d + s + 2)) for d in (1, 2) for s in (-1, 1)] + \
+         [(0, d * s, 0, float(2 * d - s + 1)) for d in (1, 2) for s in (-1, 1)] + \
+         [(0, 0, d * s, float(d)) for d in (1, 2) for s in (-1, 1)]  # integer, asymmetric
+BOX27 = [(i, j, k, float(1 + (i + 1) + 2 * (j + 1) + (k + 1) % 2)) for k in (-1, 0, 1) for j in (-1, 0, 1)
+         for i in (-1, 0, 1)]  # integer, asymmetric
+
+
+@pytest.mark.parametrize("rule,bval", [(CLAMP, 0.0), (PERIODIC, 0.0), (ZERO, 0.0), (CONST, 7.0)],
+                         ids=["clamp", "periodic", "zero", "const"])
+@pytest.mark.parametrize("points", [STAR13, BOX27, ASYM], ids=["star13", "box27", "asym7"])
+@pytest.mark.parametrize("shape", [(9, 7, 5), (6, 5, 1), (7, 1, 3), (1, 2, 4)], ids=["3d", "2d", "ny1", "nx1"])
+def test_theorem1_exact_for_general_sets(orc, rule, bval, points, shape):
+    """Theorem 1 (literal alpha/beta from u) and its chain form (vector entries outside the
+    grid by the rule applied to the vector, alpha/beta from u) both equal the recomputed
+    checksums exactly on integer data, for radius-2 and 27-point sets, every boundary
+    rule, and planes thinner than the stencil (ny = 1, nx = 1)."""
+    st = orc.Stencil(shape, points, rule, bval)
+    u = int_grid(shape, 11, hi=64)
+    C = int_grid(shape, 12, hi=16)
+    cx, cy = orc.checksums(C)
+    a, b = orc.checksums(u)
+    for _ in range(2):
+        un = orc.sweep(st, C, u)
+        an, bn = orc.checksums(un)
+        ap, bp = orc.interpolate(st, cx, cy, a, b, u)
+        np.testing.assert_array_equal(ap, an)
+        np.testing.assert_array_equal(bp, bn)
+        ap, bp = orc.interpolate_chain(st, cx, cy, a, b, u)
+        np.testing.assert_array_equal(ap, an)
+        np.testing.assert_array_equal(bp, bn)
+        u, a, b = un, an, bn
+    assert np.abs(u).max() < 2 ** 52
+
+
+def test_constant_rule_with_zero_value_is_the_empty_rule(orc):
+    shape = (11, 9, 4)
+    u = int_grid(shape, 13, hi=64)
+    C = int_grid(shape, 14, hi=16)
+    for pts in (STAR13, BOX27):
+        a = orc.sweep(orc.Stencil(shape, pts, CONST, 0.0), C, u)
+        b = orc.sweep(orc.Stencil(shape, pts, ZERO), C, u)
+        np.testing.assert_array_equal(a, b)
+
+
+def test_constant_rule_uniform_field_is_a_fixed_point(orc):
+    """u = K everywhere, outside cells K, weights summing to 1, no source: every point
+    stays K exactly; the empty rule loses mass at the faces instead."""
+    shape = (8, 7, 5)
+    K = 321.0
+    u = np.full(shape[::-1], K)
+    w = [(0, 0, 0, 1 / 2)] + [(d, 0, 0, 1 / 16) for d in (-2, -1, 1, 2)] + \
+        [(0, d, 0, 1 / 32) for d in (-2, -1, 1, 2)] + [(0, 0, d, 1 / 16) for d in (-1, 1)]
+    assert sum(p[3] for p in w) == 1.0
+    out = orc.sweep(orc.Stencil(shape, w, CONST, K), np.zeros_like(u), u)
+    np.testing.assert_array_equal(out, u)
+    assert orc.sweep(orc.Stencil(shape, w, ZERO), np.zeros_like(u), u).min() < K
+
+
+def test_constant_rule_face_closed_form(orc):
+    """u = 0 inside, K outside: a point receives K times the summed weight of its
+    neighbours that lie outside (impulse weights pin each offset)."""
+    shape = (6, 5, 4)
+    K = 2.0
+    w = dict(cc=1 / 2, cw=1 / 4, ce=1 / 8, cn=1 / 16, cs=1 / 32, cb=1 / 64, ct=1 / 128)
+    st = orc.Stencil(shape, seven(**w), CONST, K)
+    u = np.zeros(shape[::-1])
+    out = orc.sweep(st, np.zeros_like(u), u)
+    nz, ny, nx = u.shape
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                e = (w["cw"] * (x == 0) + w["ce"] * (x == nx - 1) + w["cn"] * (y == 0) + w["cs"] * (y == ny - 1)
+                     + w["cb"] * (z == 0) + w["ct"] * (z == nz - 1)) * K
+                assert out[z, y, x] == e, (z, y, x)
 
 
 # ----------------------------------------------------------- flip schedule
