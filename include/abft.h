@@ -7,7 +7,10 @@
  *   - the sweep of Eq. (1) with the 7-point HotSpot3D set S (centre, x-1, x+1, y-1,
  *     y+1, z-1, z+1) and the constant term C = sdc*P + c_amb*t_amb, with clamped
  *     boundaries (an out-of-range neighbour is the centre, Fig. 2), or periodic or
- *     empty (zero) ones (Sec. 3.3, "Dealing with Boundary Conditions");
+ *     empty (zero) ones (Sec. 3.3, "Dealing with Boundary Conditions"); or, through
+ *     option `stencils`, Eq. (1) with any set S of offsets within -2..2 (Sec. 3.1:
+ *     a 13-point star, the 27-point box, asymmetric weights), and with constant
+ *     boundaries (every cell outside the grid holds one value);
  *   - per-plane row and column checksums a[z][x] = sum_y u, b[z][y] = sum_x u
  *     (Eq. 2, 3), fused into the sweep (both every sweep, or, as Sec. 3.2 recommends,
  *     b every sweep and a only in planes where b failed: option `vectors`);
@@ -17,7 +20,9 @@
  *     at the intersection of the failing row and column, and the correction of
  *     Eq. (8) / Fig. 9, every sweep (online mode, Sec. 3);
  *   - the offline mode of Sec. 4: a checkpoint every Delta sweeps, Theorem 1 chained
- *     Delta times (Fig. 10), one comparison per window and rollback on a mismatch.
+ *     Delta times (Fig. 10), one comparison per window and rollback on a mismatch;
+ *     where the boundary terms alpha, beta do not vanish, each link of the chain takes
+ *     them from the state its sweep starts from (Theorem 1 defines them from u^t).
  *
  * Conventions for every call:
  *   - Every function returns an abft_status and never throws or aborts.  On failure
@@ -79,8 +84,17 @@ typedef enum {
 typedef enum {
   ABFT_BC_CLAMP = 0,     /* the centre point (Fig. 2) */
   ABFT_BC_PERIODIC = 1,  /* the point on the opposite face; alpha = beta = 0 in Theorem 1 */
-  ABFT_BC_ZERO = 2       /* zero ("empty" boundaries) */
+  ABFT_BC_ZERO = 2,      /* zero ("empty" boundaries) */
+  ABFT_BC_CONST = 3      /* the constant abft_options.boundary_value (a fixed temperature, say) */
 } abft_boundary;
+
+/* One point (i, j, k) of a stencil set S with its weight (Sec. 3.1's {i, j, w}, with a z
+   offset k for 3D): Eq. (1) adds w * u[z+dz][y+dy][x+dx].  Offsets within -2..2. */
+typedef struct { int32_t dx, dy, dz; float w; } abft_point;
+
+#define ABFT_MAX_POINTS 32
+/* A stencil set S of 1..ABFT_MAX_POINTS points, summed in this order. */
+typedef struct { int32_t npts; abft_point pts[ABFT_MAX_POINTS]; } abft_stencil;
 
 typedef enum {
   ABFT_EV_CORRECTED = 1,  /* Eq. (8) applied at (z, y, x); before/after hold the values */
@@ -130,6 +144,13 @@ typedef struct {
                                where b's threshold is not above a's (nx <= ny) and skips the a
                                partials and a checks; offline and unprotected steps ignore it */
   void* stream;             /* cudaStream_t used for all device work */
+  const abft_stencil* stencils; /* NULL: each grid's 7-point set from its abft_coeffs; else one set
+                               per grid (read by abft_init only, then not kept).  Grids with a
+                               general set, and contexts with ABFT_BC_CONST, run the general
+                               kernels: one launch per sweep, check and location, both checksum
+                               vectors every sweep (persistent, batch, depth, overlap and vectors
+                               do not apply) */
+  float boundary_value;     /* ABFT_BC_CONST: the value of every cell outside the grid */
 } abft_options;
 
 /* an event recorded on the device */
@@ -156,7 +177,8 @@ typedef struct {
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50
    sweeps, default tile, 64 flips per step, persistent launches, whole-column tiles for
    shallow grids, no residual tracking, depth 1, overlapped checks, batched launches,
-   clamped boundaries, both checksum vectors, NULL stream. */
+   clamped boundaries, both checksum vectors, NULL stream, no general sets, boundary
+   value 0. */
 ABFT_API void abft_default_options(abft_options* opt);
 
 /* Bytes of device workspace abft_init needs for these grids and options
@@ -180,9 +202,10 @@ ABFT_API abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n
 /* Advance every grid by n sweeps in the given mode (abft_mode).  ONLINE checks and
    corrects after each sweep (Sec. 3.2-3.5).  OFFLINE runs windows of Delta sweeps
    (the last one may be shorter), compares once per window and recomputes a
-   window from its checkpoint on a mismatch (Sec. 4); it needs boundary terms that
-   vanish (periodic boundaries, or clamped ones with cn == cs and cw == ce) and
-   returns ABFT_E_INVAL otherwise.
+   window from its checkpoint on a mismatch (Sec. 4).  Where the boundary terms do
+   not vanish (empty or constant boundaries, clamped ones with cn != cs or cw != ce,
+   general sets with offsets of two), the chain of each window takes them from every
+   sweep's input state, so such windows run one sweep per launch.
    Synchronises the stream at the end.  Errors: ABFT_E_INVAL, ABFT_E_CUDA,
    ABFT_E_TIMEOUT, ABFT_E_UNCORRECTABLE, ABFT_E_TRUNCATED (events dropped; the
    sweeps still completed). */
@@ -190,7 +213,9 @@ ABFT_API abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode);
 
 /* Theorem 2 on demand: recompute the checksums of the current state and compare
    them with the interpolated ones (chained over the sweeps made since the last
-   verified state, Sec. 4.1).  *n_mismatch receives the number of failing entries. */
+   verified state, Sec. 4.1).  *n_mismatch receives the number of failing entries.
+   More than one sweep past the verified state needs vanishing boundary terms (the
+   intermediate states are gone): ABFT_E_INVAL otherwise. */
 ABFT_API abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch);
 
 /* Correct what the last abft_verify found: Eq. (8) at single row/column

@@ -16,7 +16,8 @@ from . import build as _build
 
 MODE_NONE, MODE_ONLINE, MODE_OFFLINE = 0, 1, 2
 ACC_FP32, ACC_TWOSUM, ACC_FP64 = 0, 1, 2
-BC_CLAMP, BC_PERIODIC, BC_ZERO = 0, 1, 2
+BC_CLAMP, BC_PERIODIC, BC_ZERO, BC_CONST = 0, 1, 2, 3
+MAX_POINTS = 32
 EV_CORRECTED, EV_RECOMPUTED, EV_ROLLBACK = 1, 2, 3
 KERNEL_KINDS = ("sweep_plain", "sweep_protected", "check_online", "check_offline", "chain", "other",
                 "persistent_plain", "persistent_protected")
@@ -46,7 +47,28 @@ class abft_options(ct.Structure):
                 ("max_flips_per_step", ct.c_int32), ("persistent", ct.c_int32), ("shallow", ct.c_int32),
                 ("track_residual", ct.c_int32), ("depth", ct.c_int32), ("overlap", ct.c_int32),
                 ("batch", ct.c_int32), ("boundary", ct.c_int32), ("vectors", ct.c_int32),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("stencils", ct.c_void_p), ("boundary_value", ct.c_float)]
+
+
+class abft_point(ct.Structure):
+    _fields_ = [("dx", ct.c_int32), ("dy", ct.c_int32), ("dz", ct.c_int32), ("w", ct.c_float)]
+
+
+class abft_stencil(ct.Structure):
+    _fields_ = [("npts", ct.c_int32), ("pts", abft_point * MAX_POINTS)]
+
+
+def stencil_array(sets):
+    """ctypes array of abft_stencil from per-grid lists of (dx, dy, dz, w)."""
+    arr = (abft_stencil * len(sets))()
+    for i, pts in enumerate(sets):
+        pts = list(pts)
+        if not 1 <= len(pts) <= MAX_POINTS:
+            raise ValueError(f"a stencil set needs 1..{MAX_POINTS} points")
+        arr[i].npts = len(pts)
+        for k, (dx, dy, dz, w) in enumerate(pts):
+            arr[i].pts[k] = abft_point(int(dx), int(dy), int(dz), float(w))
+    return arr
 
 
 class abft_counters(ct.Structure):
@@ -260,7 +282,9 @@ class Context:
 
     Methods are named after the C calls they wrap (abft_step -> step, ...)."""
 
-    def __init__(self, shapes, temps, powers, coeffs, *, device=None, stream=None, **opt_kw):
+    def __init__(self, shapes, temps, powers, coeffs, *, device=None, stream=None, stencils=None, **opt_kw):
+        """stencils: None (each grid's 7-point set from its coefficients) or one list of
+        (dx, dy, dz, w) per grid (a general set S of Eq. 1, offsets within -2..2)."""
         import torch
         self._torch = torch
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -271,6 +295,12 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opt = abft_default_options(**opt_kw)
         opt.stream = self.stream.cuda_stream
+        sarr = None
+        if stencils is not None:
+            if len(stencils) != n:
+                raise ValueError("one stencil set per grid")
+            sarr = stencil_array(stencils)
+            opt.stencils = ct.cast(sarr, ct.c_void_p)
         self.opt = opt
         nbytes = abft_workspace_bytes(self.shapes, opt)
         if nbytes == 0:
@@ -290,6 +320,8 @@ class Context:
         if st != 0:
             raise AbftError(st, "abft_init failed")
         self._keep.clear()
+        del sarr  # abft_init copied the sets
+        opt.stencils = None
         self.h = h
 
     def _ptr(self, a):

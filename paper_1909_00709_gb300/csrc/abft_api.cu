@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -34,7 +35,7 @@ struct Bump {
 };
 
 struct GridPlan {
-  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx, tdirty;
+  size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx, tdirty, gs;
 };
 
 // per-launch control words of a grid: fails[3], redo, nbz, bar, bars[3] (zeroed before
@@ -76,7 +77,7 @@ bool valid_options(const abft_options& o) {
          (o.persistent == 0 || o.persistent == 1) && (o.shallow == 0 || o.shallow == 1) &&
          (o.track_residual == 0 || o.track_residual == 1) && (o.batch == 0 || o.batch == 1) &&
          o.depth >= 1 && o.depth <= 4 && (o.overlap == 0 || o.overlap == 1) && o.boundary >= ABFT_BC_CLAMP &&
-         o.boundary <= ABFT_BC_ZERO && (o.vectors == 1 || o.vectors == 2);
+         o.boundary <= ABFT_BC_CONST && (o.vectors == 1 || o.vectors == 2) && std::isfinite(o.boundary_value);
 }
 
 bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
@@ -105,6 +106,7 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     p.fcnt = b.take((size_t)2 * G.nz * sizeof(int));
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
     p.tdirty = b.take(2 * ntx * nty * sizeof(int));
+    p.gs = b.take(sizeof(GenSten));
   }
   P->ctrl = b.take(sizeof(DevCtrl));
   P->gctrl = b.take(sizeof(DevGridCtrl) * n);
@@ -279,6 +281,11 @@ struct abft_ctx {
   std::vector<CUtensorMap> tm_tb;  // temporal blocking (depth >= 2): u[0..2], C per grid
   std::vector<int> cur, ref;
   std::vector<int64_t> ref_step;
+  // general stencil sets (general.cu): every grid's set as a GenSten (the 7-point set
+  // too, for per-step chains); `general`: the context sweeps with the general kernels
+  bool general = false;
+  std::vector<GenSten> gen;
+  std::vector<char> vanish;    // Theorem 1's boundary terms vanish for the grid's set and rule
   std::vector<char> ck_valid;  // A/B[cur] are the current state's checksums: 0 no, 1 both, 2 only B
   std::vector<char> ref_ck;    // the same for A/B[ref], the verified state
   int64_t step = 0;
@@ -402,6 +409,60 @@ int other_than(int a, int b) {
 // equal, never for empty ones (their terms hold the edge rows themselves)
 bool offline_capable(const abft_coeffs& c, int bc) {
   return bc == ABFT_BC_PERIODIC || (bc == ABFT_BC_CLAMP && c.cn == c.cs && c.cw == c.ce);
+}
+
+// the chain of a grid's offline windows: Eq. (6)/(7) up front (7-point kernels, terms
+// vanish), or one link per sweep with the terms of the sweep's input state
+bool simple_chain(const abft_ctx* ctx, int gi) {
+  return !ctx->general && offline_capable(ctx->co[gi], ctx->opt.boundary);
+}
+
+// the set S of grid gi: the caller's general set, or the 7-point set of its coefficients
+// (Eq. 1's order: centre, x-1, x+1, y-1, y+1, z-1, z+1); false for an invalid set
+bool build_gen(const abft_options& o, const abft_coeffs& c, int gi, GenSten* s) {
+  memset(s, 0, sizeof *s);
+  if (o.stencils) {
+    const abft_stencil& st = o.stencils[gi];
+    if (st.npts < 1 || st.npts > kGenMaxPts) return false;
+    s->npts = st.npts;
+    for (int k = 0; k < st.npts; ++k) {
+      const abft_point& p = st.pts[k];
+      if (std::abs(p.dx) > kGenRadius || std::abs(p.dy) > kGenRadius || std::abs(p.dz) > kGenRadius ||
+          !std::isfinite(p.w))
+        return false;
+      s->dx[k] = p.dx; s->dy[k] = p.dy; s->dz[k] = p.dz; s->w[k] = p.w;
+      s->r = std::max({s->r, std::abs(p.dx), std::abs(p.dy), std::abs(p.dz)});
+    }
+    return true;
+  }
+  const int off[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  const float w[7] = {c.cc, c.cw, c.ce, c.cn, c.cs, c.cb, c.ct};
+  s->npts = 7;
+  s->r = 1;
+  for (int k = 0; k < 7; ++k) {
+    s->dx[k] = off[k][0]; s->dy[k] = off[k][1]; s->dz[k] = off[k][2]; s->w[k] = w[k];
+  }
+  return true;
+}
+
+// Theorem 1's alpha, beta vanish: periodic boundaries; clamped ones when every point has
+// an equal-weight partner mirrored in x and one mirrored in y and no in-plane offset
+// exceeds one (offsets of two leave 2u_0 - u_{n-2} - u_{n-1}); never for empty or
+// constant boundaries
+bool gen_vanish(const GenSten& s, int bc) {
+  if (bc == ABFT_BC_PERIODIC) return true;
+  if (bc != ABFT_BC_CLAMP) return false;
+  for (int k = 0; k < s.npts; ++k) {
+    if (std::abs(s.dx[k]) > 1 || std::abs(s.dy[k]) > 1) return false;
+    bool mx = false, my = false;
+    for (int m = 0; m < s.npts; ++m) {
+      if (s.dz[m] != s.dz[k] || s.w[m] != s.w[k]) continue;
+      if (s.dx[m] == -s.dx[k] && s.dy[m] == s.dy[k]) mx = true;
+      if (s.dx[m] == s.dx[k] && s.dy[m] == -s.dy[k]) my = true;
+    }
+    if (!mx || !my) return false;
+  }
+  return true;
 }
 
 // upload the flips of sweeps [t0, t0 + n) (n <= kSchedSteps); returns the number of
@@ -560,6 +621,25 @@ abft_status sweep_all(abft_ctx* ctx, int mode) {
   for (int gi = 0; gi < ctx->n; ++gi) {
     const GridDev& g = ctx->g[gi];
     const int in = ctx->cur[gi];
+    if (ctx->general) {  // any set S, any boundary rule (general.cu)
+      const int r = ctx->gen[gi].r;
+      if (mode == ABFT_MODE_ONLINE) {
+        const int out = (in + 1) % 3;
+        CK(run(ctx, kKSweepProt, [&] { return launch_sweep_gen(L, g, r, in, out, true); }));
+        CK(run(ctx, kKCheckOnline, [&] { return launch_check_gen(L, g, in, out); }));
+        CK(run(ctx, kKOther, [&] { return launch_resolve_gen(L, g, in, out, ctx->step); }));
+        ctx->cur[gi] = out;
+        ctx->ref[gi] = out;
+        ctx->ref_step[gi] = ctx->step + 1;
+        ctx->ck_valid[gi] = ctx->ref_ck[gi] = 1;
+      } else {
+        const int out = other_than(in, ctx->ref[gi]);
+        CK(run(ctx, kKSweepPlain, [&] { return launch_sweep_gen(L, g, r, in, out, false); }));
+        ctx->cur[gi] = out;
+        ctx->ck_valid[gi] = 0;
+      }
+      continue;
+    }
     if (mode == ABFT_MODE_ONLINE) {
       const int out = (in + 1) % 3;  // the verified state moves with every sweep
       CK(run(ctx, kKSweepProt, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, true); }));
@@ -937,7 +1017,9 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   abft_status s = clear_verdicts(ctx);
   if (s) return s;
   auto run_window = [&](const std::vector<int>& which) -> abft_status {
-    const int depth = ctx->opt.depth;
+    bool all_simple = true;  // per-step chains need every intermediate state
+    for (int gi : which) all_simple = all_simple && simple_chain(ctx, gi);
+    const int depth = all_simple ? ctx->opt.depth : 1;
     for (int64_t k = 0; k < d; ++k) {
       if (depth >= 2 && d - 1 - k >= depth) {  // unprotected sweeps of the window, temporally blocked
         for (int gi : which) {
@@ -955,8 +1037,19 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
         const GridDev& g = ctx->g[gi];
         const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
         const bool last = k == d - 1;
-        CK(run(ctx, last ? kKSweepProt : kKSweepPlain,
-               [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, last); }));
+        if (!simple_chain(ctx, gi)) {  // link k of the chain, with the terms of this sweep's input
+          const double* a_in = k == 0 ? g.A[ctx->ref[gi]] : g.AP[(k - 1) & 1];
+          const double* b_in = k == 0 ? g.B[ctx->ref[gi]] : g.BP[(k - 1) & 1];
+          CK(run(ctx, kKChain,
+                 [&] { return launch_chain_gen(L, g, a_in, b_in, g.u[in], g.AP[k & 1], g.BP[k & 1]); }));
+        }
+        if (ctx->general) {
+          const int r = ctx->gen[gi].r;
+          CK(run(ctx, last ? kKSweepProt : kKSweepPlain, [&] { return launch_sweep_gen(L, g, r, in, out, last); }));
+        } else {
+          CK(run(ctx, last ? kKSweepProt : kKSweepPlain,
+                 [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, last); }));
+        }
         ctx->cur[gi] = out;
       }
     }
@@ -972,6 +1065,7 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   std::vector<int> all(ctx->n);
   for (int gi = 0; gi < ctx->n; ++gi) {
     all[gi] = gi;
+    if (!simple_chain(ctx, gi)) continue;  // chained sweep by sweep inside the window
     int slot;
     s = chain(ctx, gi, ctx->g[gi].A[ctx->ref[gi]], ctx->g[gi].B[ctx->ref[gi]], d, &slot);
     if (s) return s;
@@ -1129,6 +1223,27 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   // temporal blocking recomputes halo cells level by level, which the clamped rule
   // allows locally; other boundaries sweep one level at a time
   if (opt->boundary != ABFT_BC_CLAMP) ctx->opt.depth = 1;
+  // general sets and constant boundaries run the general kernels: one launch per sweep,
+  // check and location, both checksum vectors
+  ctx->general = opt->stencils != nullptr || opt->boundary == ABFT_BC_CONST;
+  ctx->opt.stencils = nullptr;  // not kept past this call
+  if (ctx->general) {
+    ctx->opt.depth = 1;
+    ctx->opt.persistent = 0;
+    ctx->opt.batch = 0;
+    ctx->opt.overlap = 0;
+    ctx->opt.vectors = 2;
+  }
+  ctx->gen.resize(n_grids);
+  ctx->vanish.resize(n_grids);
+  for (int i = 0; i < n_grids; ++i) {
+    if (!build_gen(*opt, coeffs[i], i, &ctx->gen[i])) {
+      fail(ctx, ABFT_E_INVAL, "grid %d: a stencil set needs 1..%d points with offsets within -%d..%d", i,
+           kGenMaxPts, kGenRadius, kGenRadius);
+      return bail(ABFT_E_INVAL);
+    }
+    ctx->vanish[i] = gen_vanish(ctx->gen[i], opt->boundary);
+  }
   ctx->stream = (cudaStream_t)opt->stream;
   ctx->n = n_grids;
   ctx->grids.assign(grids, grids + n_grids);
@@ -1172,7 +1287,9 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.acc = opt->acc;
     g.gid = i;
     g.bc = opt->boundary;
-    g.vec = opt->vectors;
+    g.vec = ctx->opt.vectors;
+    g.bval = opt->boundary_value;
+    g.gs = (const GenSten*)(ws + p.gs);
     g.eps = opt->eps;
     const abft_coeffs& c = coeffs[i];
     g.k = Coef{c.cc, c.cw, c.ce, c.cn, c.cs, c.cb, c.ct};
@@ -1221,6 +1338,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     const size_t rows = (size_t)g.ny * g.nz;
     CKI(cudaMemcpy2DAsync(g.u[0], g.px * 4, temp[i], (size_t)g.nx * 4, (size_t)g.nx * 4, rows, cudaMemcpyDefault, s));
     CKI(cudaMemcpy2DAsync(g.C, g.px * 4, power[i], (size_t)g.nx * 4, (size_t)g.nx * 4, rows, cudaMemcpyDefault, s));
+    CKI(cudaMemcpyAsync((void*)g.gs, &ctx->gen[i], sizeof(GenSten), cudaMemcpyHostToDevice, s));
     CKI(run(ctx, kKOther, [&] { return launch_source_term(L, g, coeffs[i]); }));
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.C, g.cx, g.cy); }));
     CKI(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[0], g.A[0], g.B[0]); }));
@@ -1281,12 +1399,6 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
   if (!ctx) return ABFT_E_INVAL;
   if (n < 0 || mode < 0 || mode > 2) return fail(ctx, ABFT_E_INVAL, "bad step count or mode");
   if (ctx->status_seen & kStTimeout) return fail(ctx, ABFT_E_TIMEOUT, "context poisoned by an earlier timeout");
-  if (mode == ABFT_MODE_OFFLINE)
-    for (int gi = 0; gi < ctx->n; ++gi)
-      if (!offline_capable(ctx->co[gi], ctx->opt.boundary))
-        return fail(ctx, ABFT_E_INVAL,
-                    "offline mode needs vanishing boundary terms: periodic, or clamped with cn == cs and cw == ce "
-                    "(grid %d)", gi);
   ctx->verified = false;
   const int64_t t_end = ctx->step + n;
   abft_status s = ABFT_OK;
@@ -1296,7 +1408,8 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
     if (mode == ABFT_MODE_OFFLINE) {
       const int64_t delta = std::max<int64_t>(ctx->opt.delta, 1);
       persist_off = ctx->opt.persistent != 0;
-      for (int gi = 0; gi < ctx->n && persist_off; ++gi) persist_off = persistent_offline_fits(ctx->g[gi]);
+      for (int gi = 0; gi < ctx->n && persist_off; ++gi)
+        persist_off = persistent_offline_fits(ctx->g[gi]) && simple_chain(ctx, gi);
       if (persist_off) {
         if (want > delta && want < t_end - ctx->step) want -= want % delta;  // whole windows per launch
       } else {
@@ -1366,8 +1479,11 @@ abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
     const int c = ctx->cur[gi], r = ctx->ref[gi];
     const int64_t d = ctx->step - ctx->ref_step[gi];
     ctx->v_dist[gi] = d;
-    if (d > 0 && !offline_capable(ctx->co[gi], ctx->opt.boundary))
-      return fail(ctx, ABFT_E_INVAL, "chained verification needs vanishing boundary terms (grid %d)", gi);
+    const bool simple = simple_chain(ctx, gi);
+    if (d > 1 && !simple && !ctx->vanish[gi])
+      return fail(ctx, ABFT_E_INVAL,
+                  "verification %lld sweeps past the verified state needs vanishing boundary terms (grid %d)",
+                  (long long)d, gi);
     if (ctx->ref_ck[gi] != 1) {  // one-vector checks left a of the verified state unsummed
       CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[r], g.A[r], g.B[r]); }));
       ctx->ref_ck[gi] = 1;
@@ -1376,12 +1492,21 @@ abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
     CK(run(ctx, kKOther, [&] { return launch_checksums(L, g, g.u[c], g.AP[2], g.BP[2]); }));
     const double* pa = g.A[r];
     const double* pb = g.B[r];
-    if (d > 0) {
+    if (d > 0 && simple) {
       int slot;
       s = chain(ctx, gi, g.A[r], g.B[r], d, &slot);
       if (s) return s;
       pa = g.AP[slot];
       pb = g.BP[slot];
+    } else if (d > 0) {  // one sweep: the terms of the verified state; more: the terms vanish
+      for (int64_t k = 0; k < d; ++k) {
+        const double* a_in = k == 0 ? g.A[r] : g.AP[(k - 1) & 1];
+        const double* b_in = k == 0 ? g.B[r] : g.BP[(k - 1) & 1];
+        const float* us = d == 1 ? g.u[r] : nullptr;
+        CK(run(ctx, kKChain, [&] { return launch_chain_gen(L, g, a_in, b_in, us, g.AP[k & 1], g.BP[k & 1]); }));
+      }
+      pa = g.AP[(d - 1) & 1];
+      pb = g.BP[(d - 1) & 1];
     }
     CK(run(ctx, kKCheckOffline, [&] { return launch_compare(L, g, pa, pb, g.AP[2], g.BP[2]); }));
   }
@@ -1428,7 +1553,13 @@ abft_status abft_correct(abft_ctx* ctx, int64_t* n_fixed) {
       ctx->cur[gi] = ctx->ref[gi];
       for (int64_t k = 0; k < d; ++k) {
         const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
-        CK(run(ctx, kKSweepPlain, [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, false); }));
+        if (ctx->general) {
+          const int rr = ctx->gen[gi].r;
+          CK(run(ctx, kKSweepPlain, [&] { return launch_sweep_gen(L, g, rr, in, out, false); }));
+        } else {
+          CK(run(ctx, kKSweepPlain,
+                 [&] { return launch_sweep(L, g, ctx->tm_u[3 * gi + in], ctx->tm_c[gi], in, out, false); }));
+        }
         ctx->cur[gi] = out;
       }
       s = set_inject_enabled(ctx, 1);

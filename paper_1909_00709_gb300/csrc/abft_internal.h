@@ -38,6 +38,17 @@ struct Coef {
   float cc, cw, ce, cn, cs, cb, ct;
 };
 
+// A general stencil set S of Eq. (1) (Sec. 3.1), offsets within -2..2 on every axis,
+// in the order the update sums them; device copy per grid (the general path).
+constexpr int kGenMaxPts = 32;  // ABFT_MAX_POINTS
+constexpr int kGenRadius = 2;
+struct GenSten {
+  int npts;
+  int r;  // largest |offset| over the set (1 or 2; 0 for a centre-only set)
+  int dx[kGenMaxPts], dy[kGenMaxPts], dz[kGenMaxPts];
+  float w[kGenMaxPts];
+};
+
 // device-resident control block of a context
 struct DevCtrl {
   unsigned int status;
@@ -81,7 +92,9 @@ struct GridDev {
   int gid;
   int bc;                   // abft_boundary: what a neighbour outside the grid reads
   int vec;                  // checksum vectors the online check tests every sweep (2: a and b; 1: b)
+  float bval;               // ABFT_BC_CONST: the value of every cell outside the grid
   Coef k;
+  const GenSten* gs;        // the grid's stencil set as a general set (device memory)
   double eps;
   float* u[3];              // state buffers
   float* C;                 // constant term, same pitch
@@ -175,6 +188,19 @@ bool persistent_offline_fits(const GridDev& g);
 bool persistent_fits(const GridDev& g, bool prot);
 cudaError_t launch_correct_planes(const Launch& L, const GridDev& g, int cur, const double* ap,
                                   const double* bp);
+
+// ------------------------------------------------------------ general stencil sets
+// Eq. (1) with any set S of radius <= 2 and every boundary rule (general.cu): the sweep
+// with fused partial checksums (same partial layout as the 7-point tiles, so the
+// reductions of check.cu apply), the online check (Theorem 1 with literal boundary
+// terms), location and correction, and one link of an offline chain with per-step
+// boundary terms (u: the state the step starts from; nullptr when the terms vanish).
+int gen_sweep_smem(const GridDev& g, int r);
+cudaError_t launch_sweep_gen(const Launch& L, const GridDev& g, int r, int in, int out, bool prot);
+cudaError_t launch_check_gen(const Launch& L, const GridDev& g, int in, int out);
+cudaError_t launch_resolve_gen(const Launch& L, const GridDev& g, int in, int out, long long step);
+cudaError_t launch_chain_gen(const Launch& L, const GridDev& g, const double* a_in, const double* b_in,
+                             const float* u, double* a_out, double* b_out);
 
 // ------------------------------------------------------------ temporal blocking
 // k (2..4) unprotected sweeps in one pass; maps with boxes of 136 columns by 8 + 2k rows

@@ -244,24 +244,33 @@ static __device__ void correct_point(const GridDev& g, int z, int ex, int ey, fl
   __syncthreads();
 }
 
+// The point update a recomputation uses: Eq. (1) with the 7-point set of the sweep
+// kernels (point_update).  The general-stencil path passes its own (any set S).
+struct SevenPointUpdate {
+  __device__ __forceinline__ static float at(const GridDev& g, const float* u, int z, int y, int x) {
+    return point_update(g, u, z, y, x);
+  }
+};
+
 // Recompute rows fb / columns fa of plane z from the intact previous state uin
 // (whole plane when `all`), then sum the plane's checksums again.
+template <class PU = SevenPointUpdate>
 static __device__ void recompute_lines(const GridDev& g, int z, const float* uin, float* u, double* A, double* B,
                                 bool all, long long step, DevCtrl* ctrl, abft_event* ev, ResolveSmem& sm) {
   const size_t pl = (size_t)z * g.ny * g.px;
   if (all) {
     for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
       const int y = i / g.nx, x = i - y * g.nx;
-      u[pl + (size_t)y * g.px + x] = point_update(g, uin, z, y, x);
+      u[pl + (size_t)y * g.px + x] = PU::at(g, uin, z, y, x);
     }
   } else {
     for (int k = 0; k < sm.nb; ++k)
       for (int x = threadIdx.x; x < g.nx; x += blockDim.x)
-        u[pl + (size_t)sm.fb[k] * g.px + x] = point_update(g, uin, z, sm.fb[k], x);
+        u[pl + (size_t)sm.fb[k] * g.px + x] = PU::at(g, uin, z, sm.fb[k], x);
     __syncthreads();
     for (int k = 0; k < sm.na; ++k)
       for (int y = threadIdx.x; y < g.ny; y += blockDim.x)
-        u[pl + (size_t)y * g.px + sm.fa[k]] = point_update(g, uin, z, y, sm.fa[k]);
+        u[pl + (size_t)y * g.px + sm.fa[k]] = PU::at(g, uin, z, y, sm.fa[k]);
   }
   __syncthreads();
   // the plane's checksums again in compensated FP32 (TwoSum pairs widened once, as the
@@ -424,6 +433,7 @@ static __device__ void demand_a(const GridDev& g, const float* uin, const float*
   __syncthreads();
 }
 
+template <class PU = SevenPointUpdate>
 static __device__ void resolve_plane(ResolveSmem& sm, const GridDev& g, const float* uin, float* u, double* A,
                                      double* B, const double* ap, const double* bp, long long step, DevCtrl* ctrl,
                                      abft_event* ev, unsigned long long* unresolved, int z, bool a_summed = false) {
@@ -452,7 +462,7 @@ static __device__ void resolve_plane(ResolveSmem& sm, const GridDev& g, const fl
     correct_point(g, z, sm.fa[0], sm.fb[0], u, A, B, ap, bp, step, ctrl, ev, sm);
   } else if (uin != nullptr) {
     if (overflow && threadIdx.x == 0) set_status(ctrl, kStFailOverflow);
-    recompute_lines(g, z, uin, u, A, B, overflow, step, ctrl, ev, sm);
+    recompute_lines<PU>(g, z, uin, u, A, B, overflow, step, ctrl, ev, sm);
   } else if (threadIdx.x == 0) {
     atomicAdd(unresolved, 1ull);
   }

@@ -46,6 +46,23 @@ def test_struct_layouts_match_numpy_views(abi):
         assert getattr(abi.abft_flip, name).offset == off[1]
 
 
+def test_stencil_structs_match_the_header(abi):
+    """abft_point is 16 bytes (three int32 offsets and a float weight); abft_stencil holds a
+    count and ABFT_MAX_POINTS points; the options end with the stencil pointer and the
+    constant boundary value, as include/abft.h declares."""
+    assert ct.sizeof(abi.abft_point) == 16
+    assert abi.abft_stencil.pts.offset == 4
+    assert ct.sizeof(abi.abft_stencil) == 4 + 16 * abi.MAX_POINTS
+    hdr = open(os.path.join(ROOT, "include", "abft.h")).read()
+    assert f"#define ABFT_MAX_POINTS {abi.MAX_POINTS}" in hdr
+    names = [f[0] for f in abi.abft_options._fields_]
+    assert names[-3:] == ["stream", "stencils", "boundary_value"]
+    arr = abi.stencil_array([[(0, 0, 0, 0.5), (-2, 1, 0, 0.25)]])
+    assert arr[0].npts == 2 and arr[0].pts[1].dx == -2 and arr[0].pts[1].dy == 1 and arr[0].pts[1].w == 0.25
+    with pytest.raises(ValueError):
+        abi.stencil_array([[]])
+
+
 def test_default_options_follow_table1(abi):
     o = abi.abft_default_options()
     assert o.eps == 1e-5 and o.delta == 16
@@ -58,11 +75,16 @@ def test_workspace_bytes_validates(abi):
     assert abi.abft_workspace_bytes([(0, 64, 8)], o) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(tile_y=12)) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(eps=-1.0)) == 0
-    # boundary rules 0..2 (clamped, periodic, zero); the field sits where the C struct has it
+    # boundary rules 0..3 (clamped, periodic, zero, constant); the field sits where the C
+    # struct has it
     assert o.boundary == abi.BC_CLAMP
-    for bc in (abi.BC_PERIODIC, abi.BC_ZERO):
+    for bc in (abi.BC_PERIODIC, abi.BC_ZERO, abi.BC_CONST):
         assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=bc)) > 0
-    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=3)) == 0
+    assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=4)) == 0
+    # the constant boundary's value must be finite (the last field of the C struct)
+    assert o.boundary_value == 0.0 and o.stencils is None
+    assert abi.abft_workspace_bytes([(64, 64, 8)],
+                                    abi.abft_default_options(boundary=abi.BC_CONST, boundary_value=float("nan"))) == 0
     assert abi.abft_workspace_bytes([(64, 64, 8)], abi.abft_default_options(boundary=-1)) == 0
     # checksum vectors of the online check: 2 (default) or 1; the field after `boundary`
     assert o.vectors == 2

@@ -51,6 +51,29 @@ def timed_oracle(orc, *a, **kw):
     return r
 
 
+def unhandled_flip_mask(shape, flips, events, last_step, min_bit=6):
+    """Points a flip that no event removed may have reached by the end of the run (its
+    stencil cone, one cell per sweep in each direction), for bits >= min_bit.  Such a flip
+    stays in both grids, but the GPU flips a bit of its own FP32 value while the oracle
+    flips the FP32 image of its FP64 value; where a rounding difference of a few ulps
+    carries through bit k, the two perturbations differ by 2 * 2^(k - 15) K near 330 K
+    (below 1e-5 relative for k < 6)."""
+    nx, ny, nz = shape
+    handled = set()
+    for e in events:
+        t, z, y, x = (int(e[k]) for k in ("step", "z", "y", "x"))
+        handled.add((t, z, y, x))  # a point (kind 1) or a line (kind 2, y or x = -1)
+    keep = np.ones((nz, ny, nx), dtype=bool)
+    for f in flips:
+        t, z, y, x, b = (int(f[k]) for k in ("step", "z", "y", "x", "bit"))
+        if b < min_bit or (t, z, y, x) in handled or (t, z, y, -1) in handled or (t, z, -1, x) in handled \
+                or (t, z, -1, -1) in handled:
+            continue
+        r = int(last_step - t)
+        keep[max(0, z - r):z + r + 1, max(0, y - r):y + r + 1, max(0, x - r):x + r + 1] = False
+    return keep
+
+
 def marginal_mask(shape, marginal, last_step):
     """Points whose value may differ because a (sweep, plane) pair fell inside the
     oracle's guard band (detection there is decided by rounding): the plane and every
@@ -186,7 +209,9 @@ def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc, ora
     and corrects (or recomputes) what the oracle does.
 
     Values: the window (rolled back, recomputed without flips) within 1e-5.  After the
-    online sweeps, a point written by Eq. (8) carries the rounding error of the
+    online sweeps, points a sub-threshold flip may have reached are left out (see
+    unhandled_flip_mask: a few ulps of rounding difference decide which way the flipped
+    bit moves each side's value).  A point written by Eq. (8) carries the rounding error of the
     interpolated checksum it was computed from, while the oracle's checksums are exact.
     With compensated (TwoSum) tile sums that error is the FP32 sweep's own rounding summed
     along a line (about sqrt(n) half-ulps of the line's 1024 values, a few 1e-4 K on
@@ -214,8 +239,10 @@ def test_1024x1024x256_offline_window_then_online_at_workload_rate(abi, orc, ora
     assert len(o) > 100
     assert g == o
     keep = marginal_mask(SHAPE4, r_on["marginal"], 2 * DELTA4 - 1)
+    keep &= unhandled_flip_mask(SHAPE4, s_on, r_on["events"], 2 * DELTA4 - 1)
     err = rel_err(got[keep], r_on["u"][keep])
-    print(f"  acc {acc}: max rel err {err:.2e} (bound {tol:.0e})")
+    print(f"  acc {acc}: max rel err {err:.2e} (bound {tol:.0e}) on {keep.mean():.1%} of the grid")
+    assert keep.mean() > 0.5
     assert err < tol
 
 
