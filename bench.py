@@ -73,6 +73,10 @@ def parse():
                    help="mode of the protected job of --profile captures (1 online, 2 offline)")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
                    help="abft_options field for --profile captures (e.g. tile_y=16)")
+    p.add_argument("--case", default="headline", choices=list(PROFILE_CASES),
+                   help="workload of a --profile capture: headline (persistent online and plain kernels), "
+                        "offline, large (per-launch online with overlapped checks and repairs), checkonline "
+                        "(plain-load check of a grid with > 256 tiles along y), batch, tblock, general")
     p.add_argument("--vectors", type=int, default=1, choices=[1, 2],
                    help="checksum vectors of the online check: 1 = b every sweep, a where b failed "
                         "(the paper's recommendation, Sec. 3.2); 2 = both every sweep")
@@ -730,6 +734,69 @@ def side_runs(dev, stream, flush, hbm_peak):
                                        "frac": {k: v * BYTES_PER_UPDATE / hbm_peak for k, v in large.items()}}}}
 
 
+PROFILE_CASES = ("headline", "offline", "large", "checkonline", "batch", "tblock", "general")
+
+
+def run_profile_case(args):
+    """The workloads of the per-kernel ncu captures: each exercises one family of kernels
+    for a few launches on a grid larger than L2 (a few hundred MB on the device)."""
+    import math
+    import torch
+    from paper_1909_00709_gb300 import abi, inputs
+
+    def ctx(shapes, seeds, **opt):
+        ts, ps, cs = [], [], []
+        for sh, sd in zip(shapes, seeds):
+            t, p = inputs.grid_inputs(*sh, seed=sd)
+            ts.append(t)
+            ps.append(p)
+            cs.append(inputs.hotspot_coeffs(*sh))
+        return abi.Context(shapes, ts, ps, cs, **opt)
+
+    big = (1024, 1024, 64)
+    launches = 0
+    if args.case == "offline":  # persistent offline windows, then per-launch windows
+        for persistent in (1, 0):
+            with ctx([big], [4], persistent=persistent) as c:
+                c.inject(4, 1.0, 0xFFFFFFFF)
+                c.step(32, abi.MODE_OFFLINE)
+                launches += c.counters()["kernel_launches"]
+        with ctx([(512, 512, 8)], [1]) as c:
+            c.step(64, abi.MODE_OFFLINE)
+            launches += c.counters()["kernel_launches"]
+    elif args.case == "large":  # per-launch online: overlapped checks, repairs, both vector settings
+        for vec in (2, 1):
+            with ctx([big], [4], vectors=vec, max_flips_per_step=64) as c:
+                c.inject(4, 2.0, 0xFFFFFFFF)
+                c.step(8, abi.MODE_ONLINE)
+                launches += c.counters()["kernel_launches"]
+    elif args.case == "checkonline":  # > 256 tiles along y: the plain-load check kernel
+        with ctx([(256, 8192, 16)], [4], persistent=0) as c:
+            c.step(6, abi.MODE_ONLINE)
+            launches += c.counters()["kernel_launches"]
+    elif args.case == "batch":  # batched sweeps and checks over uneven grids
+        shapes = inputs.batch_shapes(16, seed=3)
+        with ctx(shapes, [1000 + i for i in range(16)], batch=1, graph_steps=0) as c:
+            c.inject(9, 0.5, 0xFFFFFFFF)
+            c.step(6, abi.MODE_ONLINE)
+            c.step(6, abi.MODE_NONE)
+            launches += c.counters()["kernel_launches"]
+    elif args.case == "tblock":  # temporally blocked unprotected passes, depth 2
+        with ctx([big], [4], depth=2, persistent=0) as c:
+            c.step(8, abi.MODE_NONE)
+            launches += c.counters()["kernel_launches"]
+    elif args.case == "general":  # a 13-point star: online with flips, then offline windows
+        star = [(0, 0, 0, 0.5)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
+               [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)] + [(0, 0, d, 0.0) for d in (-1, 1)]
+        with ctx([big], [4], stencils=[star]) as c:
+            c.inject(4, 2.0, 0xFFFFFFFF)
+            c.step(6, abi.MODE_ONLINE)
+            c.step(8, abi.MODE_OFFLINE)
+            launches += c.counters()["kernel_launches"]
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.case, "launches": launches, "points": math.prod(big)}))
+
+
 def run_profile(args, local):
     """Warm-up jobs, then one protected online job and one unprotected job; no output
     beyond one summary line.  Used as the command under ncu."""
@@ -737,6 +804,9 @@ def run_profile(args, local):
     from paper_1909_00709_gb300 import abi, inputs
     torch.cuda.set_device(local)
     abi.lib(build_if_missing=True)
+    if args.case != "headline":
+        run_profile_case(args)
+        return
     temp, power = inputs.grid_inputs(*SHAPE, seed=1)
     co = inputs.hotspot_coeffs(*SHAPE)
     opts = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
