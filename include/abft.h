@@ -128,6 +128,12 @@ typedef struct {
   int32_t depth;            /* temporal blocking: unprotected sweeps (mode NONE, and the sweeps of
                                an offline window before its last) advance `depth` (1..4) sweeps per
                                pass over the grid where a grid is swept launch by launch; 1 = off.
+                               Online checks of a single grid launched sweep by sweep (FP32
+                               checksums, boundary terms that vanish) also run in passes: each pass
+                               writes every level's partial checksums, every level is checked
+                               (Theorem 1 from the level before, Sec. 3.4), and a pass with a
+                               failing entry is recomputed sweep by sweep with the online check of
+                               every sweep, which locates, corrects and logs as single sweeps do.
                                Used with the clamped boundary only (others sweep one at a time). */
   int32_t overlap;          /* 1: a single grid checked online launch by launch (too large for the
                                persistent kernel) runs each sweep's check beside the next sweep and
@@ -172,6 +178,8 @@ typedef struct {
   int64_t rollbacks;        /* offline windows recomputed */
   int64_t flips_scheduled;  /* flips handed to the device */
   double max_residual;      /* largest passing |a'-a|/|a| so far (0 unless track_residual) */
+  int64_t passes_recomputed; /* online passes of temporal blocking (depth >= 2) whose check failed
+                               and that were recomputed sweep by sweep */
 } abft_counters;
 
 /* Fill defaults: eps 1e-5, delta 16 (Table 1), acc FP32, 4096 events, graphs of 50

@@ -73,7 +73,8 @@ def stencil_array(sets):
 
 class abft_counters(ct.Structure):
     _fields_ = [("steps_done", ct.c_int64), ("kernel_launches", ct.c_int64), ("events", ct.c_int64),
-                ("rollbacks", ct.c_int64), ("flips_scheduled", ct.c_int64), ("max_residual", ct.c_double)]
+                ("rollbacks", ct.c_int64), ("flips_scheduled", ct.c_int64), ("max_residual", ct.c_double),
+                ("passes_recomputed", ct.c_int64)]
 
 
 class abft_event(ct.Structure):

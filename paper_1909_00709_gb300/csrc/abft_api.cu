@@ -36,6 +36,7 @@ struct Bump {
 
 struct GridPlan {
   size_t u[3], C, cx, cy, A[3], B[3], AP[3], BP[3], PA, PB, PA2, PB2, fcnt, fidx, tdirty, gs;
+  size_t tbpa[4], tbpb[4];  // per-level partials of protected temporally blocked passes
 };
 
 // per-launch control words of a grid: fails[3], redo, nbz, bar, bars[3] (zeroed before
@@ -57,8 +58,14 @@ struct Plan {
 
 bool is_shallow(const abft_options& o, const abft_grid& G) { return o.shallow && G.nz <= kShallowMaxZ; }
 
-// rows per tile: streaming tiles default to 16, whole-column tiles to 8 (16 allowed)
+// contexts that sweep with the general kernels (general.cu): a general set or constant
+// boundaries
+bool general_opts(const abft_options& o) { return o.stencils != nullptr || o.boundary == ABFT_BC_CONST; }
+
+// rows per tile: streaming tiles default to 16, whole-column tiles to 8 (16 allowed); the
+// general kernels' tiles have kGenTY rows
 int pick_ty(const abft_options& o, const abft_grid& G) {
+  if (general_opts(o)) return kGenTY;
   if (is_shallow(o, G)) return o.tile_y == 16 && G.nz <= 8 ? 16 : 8;
   return o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32 ? o.tile_y : 16;
 }
@@ -107,6 +114,14 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
     p.fidx = b.take((size_t)2 * G.nz * kFCap * sizeof(int));
     p.tdirty = b.take(2 * ntx * nty * sizeof(int));
     p.gs = b.take(sizeof(GenSten));
+    // online checks with temporal blocking: FP32 partials of every level, tiles of
+    // kTbRows rows (a partials only with two checksum vectors)
+    const size_t nty8 = (G.ny + kTbRows - 1) / kTbRows;
+    for (int k = 0; k < 4; ++k) {
+      const bool lvl = o.depth >= 2 && k < o.depth;
+      p.tbpa[k] = b.take(lvl && o.vectors == 2 ? nty8 * G.nz * ntx * kTX * 4 : 0);
+      p.tbpb[k] = b.take(lvl ? ntx * G.nz * align_up(G.ny, 4) * 4 : 0);
+    }
   }
   P->ctrl = b.take(sizeof(DevCtrl));
   P->gctrl = b.take(sizeof(DevGridCtrl) * n);
@@ -286,6 +301,11 @@ struct abft_ctx {
   bool general = false;
   std::vector<GenSten> gen;
   std::vector<char> vanish;    // Theorem 1's boundary terms vanish for the grid's set and rule
+  // online checks with temporal blocking: per-level partials, and the verdict of each
+  // pass copied to pinned memory behind an event (two in flight)
+  std::vector<TbLevels> tbl;
+  unsigned long long* h_tbflag = nullptr;
+  cudaEvent_t tb_ev[2] = {nullptr, nullptr};
   std::vector<char> ck_valid;  // A/B[cur] are the current state's checksums: 0 no, 1 both, 2 only B
   std::vector<char> ref_ck;    // the same for A/B[ref], the verified state
   int64_t step = 0;
@@ -339,7 +359,7 @@ struct abft_ctx {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [unprotected, online]: graph_steps sweeps each
   // counters
-  int64_t launches = 0, rollbacks = 0, flips_scheduled = 0;
+  int64_t launches = 0, rollbacks = 0, flips_scheduled = 0, tb_redo = 0;
   unsigned status_seen = 0;
   std::string err;
 };
@@ -940,6 +960,97 @@ abft_status tb_all(abft_ctx* ctx) {
   return ABFT_OK;
 }
 
+// Online checks with temporal blocking (a single clamped grid whose boundary terms vanish,
+// FP32 checksums): passes of k = depth sweeps, each one blocked launch that also writes
+// every level's partial checksums, then one check launch per level (Theorem 1 from the
+// level before, the Sec. 3.4 test).  The verdict of a pass is read on the host one pass
+// later, while the next pass runs: a pass writes the third buffer, so the input of the
+// previous one is still intact.  A pass with a failing entry is discarded (and the one
+// launched after it) and its k sweeps are recomputed as single sweeps with the online
+// check of every sweep, which locates and corrects what failed and logs the events
+// exactly as the single-sweep online mode does.
+abft_status set_grid_step(abft_ctx* ctx, int gi, int64_t step);
+
+bool online_tb_ok(const abft_ctx* ctx) {
+  return ctx->n == 1 && ctx->opt.depth >= 2 && !ctx->general && ctx->opt.boundary == ABFT_BC_CLAMP &&
+         simple_chain(ctx, 0) && ctx->opt.acc == ABFT_ACC_FP32;
+}
+
+abft_status online_tb(abft_ctx* ctx, int64_t n) {
+  const int gi = 0, k = ctx->opt.depth;
+  const GridDev& g = ctx->g[gi];
+  const Launch L = launcher(ctx);
+  GridDev gt = g;  // the level checks' view: partials of kTbRows-row tiles
+  gt.ty = kTbRows;
+  gt.nty = (g.ny + kTbRows - 1) / kTbRows;
+  const int64_t t_end = ctx->step + n;
+  struct Pass {
+    int64_t t0 = -1;
+    int in = 0, slot = 0;
+  } prev;
+  int slot = 0;
+  abft_status s = ABFT_OK;
+  for (;;) {
+    Pass cur;
+    const bool launch = ctx->step + k <= t_end;
+    if (launch) {
+      s = ensure_checksums(ctx, gi, g.vec != 1);
+      if (s) return s;
+      const int in = ctx->cur[gi], out = (in + 1) % 3;
+      cur.t0 = ctx->step;
+      cur.in = in;
+      cur.slot = slot;
+      CK(cudaMemsetAsync(&ctx->gctrl[gi].verdict, 0, sizeof(unsigned long long), ctx->stream));
+      CK(run(ctx, kKSweepProt, [&] {
+        return launch_sweep_tb_prot(L, g, ctx->tm_tb[4 * gi + in], ctx->tm_tb[4 * gi + 3], out, k, ctx->tbl[gi]);
+      }));
+      for (int tau = 1; tau <= k; ++tau) {
+        gt.PA = ctx->tbl[gi].PA[tau - 1];
+        gt.PB = ctx->tbl[gi].PB[tau - 1];
+        const double* a_prev = tau == 1 ? g.A[in] : g.AP[tau - 2];
+        const double* b_prev = tau == 1 ? g.B[in] : g.BP[tau - 2];
+        double* a_out = tau == k ? g.A[out] : g.AP[tau - 1];
+        double* b_out = tau == k ? g.B[out] : g.BP[tau - 1];
+        CK(run(ctx, kKCheckOnline, [&] { return launch_check_tb_level(L, gt, a_prev, b_prev, a_out, b_out); }));
+      }
+      CK(cudaMemcpyAsync(&ctx->h_tbflag[slot], &ctx->gctrl[gi].verdict, sizeof(unsigned long long),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaEventRecord(ctx->tb_ev[slot], ctx->stream));
+      ctx->cur[gi] = out;
+      ctx->ref[gi] = out;
+      ctx->ref_step[gi] = ctx->step + k;
+      ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(g);
+      ctx->step += k;
+      slot ^= 1;
+    }
+    if (prev.t0 >= 0) {
+      CK(cudaEventSynchronize(ctx->tb_ev[prev.slot]));
+      if (ctx->h_tbflag[prev.slot] != 0) {  // recompute the failed pass sweep by sweep
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->cur[gi] = ctx->ref[gi] = prev.in;
+        ctx->step = ctx->ref_step[gi] = prev.t0;
+        ctx->ck_valid[gi] = ctx->ref_ck[gi] = online_ck(g);
+        s = set_grid_step(ctx, gi, prev.t0);
+        if (s) return s;
+        ++ctx->tb_redo;
+        for (int j = 0; j < k; ++j) {
+          s = sweep_all(ctx, ABFT_MODE_ONLINE);
+          if (s) return s;
+        }
+        prev.t0 = -1;
+        continue;
+      }
+    }
+    if (!launch) break;
+    prev = cur;
+  }
+  while (ctx->step < t_end) {  // a remainder shorter than a pass
+    s = sweep_all(ctx, ABFT_MODE_ONLINE);
+    if (s) return s;
+  }
+  return ABFT_OK;
+}
+
 abft_status status_from_device(abft_ctx* ctx) {
   const unsigned st = ctx->h_ctrl->status;
   ctx->status_seen |= st;
@@ -1195,6 +1306,9 @@ void abft_destroy(abft_ctx* ctx) {
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
   if (ctx->h_gctrl) cudaFreeHost(ctx->h_gctrl);
   if (ctx->h_ev) cudaFreeHost(ctx->h_ev);
+  if (ctx->h_tbflag) cudaFreeHost(ctx->h_tbflag);
+  for (cudaEvent_t e : ctx->tb_ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -1225,7 +1339,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
   if (opt->boundary != ABFT_BC_CLAMP) ctx->opt.depth = 1;
   // general sets and constant boundaries run the general kernels: one launch per sweep,
   // check and location, both checksum vectors
-  ctx->general = opt->stencils != nullptr || opt->boundary == ABFT_BC_CONST;
+  ctx->general = general_opts(*opt);
   ctx->opt.stencils = nullptr;  // not kept past this call
   if (ctx->general) {
     ctx->opt.depth = 1;
@@ -1268,6 +1382,9 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
       cudaMallocHost(&ctx->h_roles, sizeof(BatchRole) * n_grids) != cudaSuccess)
     return bail(ABFT_E_NOMEM);
   if (cudaEventCreateWithFlags(&ctx->roles_ev, cudaEventDisableTiming) != cudaSuccess) return bail(ABFT_E_CUDA);
+  if (cudaMallocHost(&ctx->h_tbflag, 2 * sizeof(unsigned long long)) != cudaSuccess) return bail(ABFT_E_NOMEM);
+  for (cudaEvent_t& e : ctx->tb_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(ABFT_E_CUDA);
   memset(ctx->h_ctrl, 0, sizeof(DevCtrl));
   memset(ctx->h_gctrl, 0, sizeof(DevGridCtrl) * n_grids);
   for (int i = 0; i < n_grids; ++i) {
@@ -1311,6 +1428,12 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     g.fidx = (int*)(ws + p.fidx);
     g.tdirty = (int*)(ws + p.tdirty);
     g.gc = ctx->gctrl + i;
+    TbLevels lvl{};
+    for (int k = 0; k < 4; ++k) {
+      lvl.PA[k] = ws + p.tbpa[k];
+      lvl.PB[k] = ws + p.tbpb[k];
+    }
+    ctx->tbl.push_back(lvl);
   }
   ctx->tm_u.resize(3 * n_grids);
   ctx->tm_c.resize(n_grids);
@@ -1454,6 +1577,11 @@ abft_status abft_step(abft_ctx* ctx, int64_t n, int32_t mode) {
           s = ensure_checksums(ctx, gi, ctx->g[gi].vec != 1);
           if (s) return s;
         }
+      if (mode == ABFT_MODE_ONLINE && online_tb_ok(ctx) && covered - k >= ctx->opt.depth) {
+        s = online_tb(ctx, covered - k);
+        if (s) return s;
+        break;
+      }
       if (mode == ABFT_MODE_ONLINE && ctx->n == 1 && ctx->opt.overlap && !ctx->timing) {
         s = online_overlap(ctx, covered - k);
         if (s) return s;
@@ -1631,6 +1759,7 @@ abft_status abft_get_counters(const abft_ctx* ctx, abft_counters* out) {
     mr = std::max(mr, v);
   }
   out->max_residual = mr;
+  out->passes_recomputed = ctx->tb_redo;
   return ABFT_OK;
 }
 

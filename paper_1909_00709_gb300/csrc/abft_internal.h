@@ -42,6 +42,7 @@ struct Coef {
 // in the order the update sums them; device copy per grid (the general path).
 constexpr int kGenMaxPts = 32;  // ABFT_MAX_POINTS
 constexpr int kGenRadius = 2;
+constexpr int kGenTY = 8;       // rows per tile of the general sweep (its partial checksums' tiles)
 struct GenSten {
   int npts;
   int r;  // largest |offset| over the set (1 or 2; 0 for a centre-only set)
@@ -208,6 +209,19 @@ constexpr int kTbRows = 8;
 cudaError_t make_tb_maps(const GridDev& g, int k, CUtensorMap tm_u[3], CUtensorMap* tm_c, char* err, size_t errlen);
 cudaError_t launch_sweep_tb(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
                             int out, int k);
+// Online checks with temporal blocking: a protected pass of k sweeps writes the FP32
+// partial checksums of every level tau (1..k) into PA[tau-1] (a, with two vectors) and
+// PB[tau-1] (b), tiles of kTbRows rows; then one check launch per level.
+struct TbLevels {
+  void* PA[4];
+  void* PB[4];
+};
+cudaError_t launch_sweep_tb_prot(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
+                                 int out, int k, const TbLevels& lp);
+// gt: the grid with PA/PB of the level and nty/ty of kTbRows-row tiles; failing entries
+// are added to gt.gc->verdict
+cudaError_t launch_check_tb_level(const Launch& L, const GridDev& gt, const double* a_prev, const double* b_prev,
+                                  double* a_out, double* b_out);
 
 // ------------------------------------------------------------ batched grids
 // Buffer roles of sweep s of one grid in a batched run that started at sweep s0.

@@ -6,11 +6,12 @@
 // otherwise), and the links of an offline chain (Fig. 10) whose boundary terms come from
 // each step's own state where they do not vanish.
 //
-// The sweep: one CTA per 128 x TY tile streams z.  Staged planes (TY + 2r rows, 136
-// columns: a 4-column, 16-byte aligned x halo that covers r <= 2) rotate through a ring
-// of 2r + 2 shared-memory slots; interior 16-byte chunks arrive by cp.async while the
-// CTA computes the previous plane, and cells outside the grid are written with the
-// boundary rule's value (clamped or wrapped index, zero, or the constant).  Every point
+// The sweep: one CTA per 128 x 8 tile (one row per warp) streams z.  Staged planes (8 + 2r
+// rows, 136 columns: a 4-column, 16-byte aligned x halo that covers r <= 2) and the
+// tile's plane of C rotate through a ring of 2r + 3 shared-memory slots, filled by
+// cp.async two planes ahead of their use: interior 16-byte chunks directly, cells outside
+// the grid by 4-byte copies of the cell the boundary rule maps them to (clamped or
+// wrapped index) or by stores of its fixed value (zero, the constant).  Every point
 // sums its set in the set's order (one FMA chain) and adds C, the same arithmetic as
 // gen_update, which the location step uses to recompute lines.  The partial checksums
 // have the layout of the 7-point tiles (b: the row's 128 values by a warp butterfly;
@@ -134,7 +135,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_ahead() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // one value added to a column partial, in the accumulation's arithmetic
@@ -152,6 +156,14 @@ __device__ __forceinline__ typename RowPart<ACC>::T col_zero() {
   return typename RowPart<ACC>::T{};
 }
 
+// Tiles of the general sweep: 128 x kGenTY (one row per warp).  A ring slot holds one
+// staged plane of u (kGenTY + 2r rows by 136 columns) and the tile's plane of C
+// (kGenTY rows by 128 columns); planes arrive kGenAhead iterations before they are
+// needed, so the copies of two planes are in flight while the CTA computes.
+constexpr int kGenAhead = 2;
+
+__host__ __device__ constexpr int gen_slot_floats(int r) { return (kGenTY + 2 * r) * kGenW + kGenTY * kTX; }
+
 template <int ACC, bool PROT>
 __global__ void __launch_bounds__(kGenThreads, 2)
     k_sweep_gen(const GridDev g, const float* __restrict__ uin, float* __restrict__ uout, int r,
@@ -164,7 +176,7 @@ __global__ void __launch_bounds__(kGenThreads, 2)
   __shared__ float s_w[kGenMaxPts];
   __shared__ int4 lf[kLocalFlips];
   __shared__ int nlf;
-  const int TY = g.ty, R = TY + 2 * r, S = 2 * r + 2, PS = R * kGenW;
+  const int R = kGenTY + 2 * r, S = 2 * r + 1 + kGenAhead, PS = gen_slot_floats(r);
   T* colp = reinterpret_cast<T*>(ring + (size_t)S * PS);  // [8 warps][128 columns] of one plane
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const GenSten* gs = g.gs;
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(kGenThreads, 2)
   sched.load(ctrl);
   const long long step = g.gc->step;
   const int txi = blockIdx.x % g.ntx, tyi = blockIdx.x / g.ntx;
-  const int x0 = txi * kTX, y0 = tyi * TY;
+  const int x0 = txi * kTX, y0 = tyi * kGenTY;
   __syncthreads();
   // this sweep's flips in the tile's output region (Sec. 5.1)
   if (sched.enabled) {
@@ -186,14 +198,17 @@ __global__ void __launch_bounds__(kGenThreads, 2)
       for (int k = sched.off[i] + tid; k < sched.off[i + 1]; k += kGenThreads) {
         const DevFlip f = sched.flips[k];
         if (f.grid == g.gid && f.target == 0 && f.x >= x0 && f.x < x0 + kTX && f.x < g.nx && f.y >= y0 &&
-            f.y < y0 + TY && f.y < g.ny && f.z >= 0 && f.z < g.nz) {
+            f.y < y0 + kGenTY && f.y < g.ny && f.z >= 0 && f.z < g.nz) {
           const int j = atomicAdd(&nlf, 1);
           if (j < kLocalFlips) lf[j] = make_int4(f.x, f.y, f.z, f.bit & 31);
           else set_status(ctrl, kStFlipOverflow);
         }
       }
   }
-  auto load_plane = [&](int p) {  // plane p (possibly outside 0..nz-1) into its slot
+  // plane p (possibly outside 0..nz-1) of u and, inside the grid, of C into its slot:
+  // 16-byte copies where a chunk lies inside the grid, 4-byte copies of the cell the
+  // rule maps an outside cell to (clamped, periodic), stores of the fixed value otherwise
+  auto load_plane = [&](int p) {
     if (p <= g.nz - 1 + r) {
       float* dst = ring + (size_t)((p + r) % S) * PS;
       for (int c = tid; c < R * kGenChunks; c += kGenThreads) {
@@ -204,20 +219,35 @@ __global__ void __launch_bounds__(kGenThreads, 2)
           cp_async16(d, uin + ((size_t)p * g.ny + gy) * g.px + gx);
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) d[e] = gen_ghost(g, uin, p, gy, gx + e);
+          for (int e = 0; e < 4; ++e) {
+            int zz = p, yy = gy, xx = gx + e;
+            if (gen_map(zz, g.nz, g.bc) && gen_map(yy, g.ny, g.bc) && gen_map(xx, g.nx, g.bc))
+              cp_async4(d + e, uin + ((size_t)zz * g.ny + yy) * g.px + xx);
+            else
+              d[e] = gen_outside(g);
+          }
+        }
+      }
+      if (p >= 0 && p < g.nz) {  // C of the tile's own points, one 16-byte chunk per thread
+        float* dc = dst + R * kGenW;
+        for (int c = tid; c < kGenTY * (kTX / 4); c += kGenThreads) {
+          const int row = c / (kTX / 4), q = c - row * (kTX / 4);
+          const int gy = y0 + row, gx = x0 + 4 * q;
+          if (gy < g.ny && gx < g.nx) cp_async16(dc + row * kTX + 4 * q, g.C + ((size_t)p * g.ny + gy) * g.px + gx);
         }
       }
     }
     cp_async_commit();  // one group per plane, empty past the last one
   };
-  for (int p = -r; p <= r; ++p) load_plane(p);
+  for (int p = -r; p <= r + kGenAhead - 1; ++p) load_plane(p);
   __syncthreads();
   const int nf = min(nlf, kLocalFlips);
   T ca[4];
+  const int row = warp, gy = y0 + row;
   for (int z = 0; z < g.nz; ++z) {
     if (tid < npts) s_koff[tid] = ((z + gs->dz[tid] + r) % S) * PS + s_off[tid];
-    load_plane(z + r + 1);
-    cp_async_wait_1();  // every plane up to z + r has landed
+    load_plane(z + r + kGenAhead);
+    cp_async_wait_ahead();  // every plane up to z + r has landed
     __syncthreads();
     if (PROT && z > 0 && tid < kTX && x0 + tid < g.nx) {  // column partials of plane z-1
       T t = colp[tid];
@@ -225,35 +255,38 @@ __global__ void __launch_bounds__(kGenThreads, 2)
       for (int w = 1; w < 8; ++w) t = RP::comb(t, colp[w * kTX + tid]);
       RP::store(g.PA, ((size_t)tyi * g.nz + (z - 1)) * g.pa_stride + x0 + tid, t);
     }
+    const float* rb = ring + (row + r) * kGenW + lane + kHaloX;  // column lane + 32 j of this row
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};  // four independent FMA chains, one per column
+    for (int k = 0; k < npts; ++k) {
+      const float w = s_w[k];
+      const float* q = rb + s_koff[k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ca[j] = col_zero<ACC>();
-    const float* Crow = g.C + (size_t)z * g.ny * g.px;
-    float* Urow = uout + (size_t)z * g.ny * g.px;
-    for (int row = warp; row < TY; row += 8) {
-      const int gy = y0 + row;
-      float m[4];
+      for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(w, q[32 * j], acc[j]);
+    }
+    const float* cs = ring + (size_t)((z + r) % S) * PS + R * kGenW + row * kTX + lane;
+    float* Urow = uout + ((size_t)z * g.ny + gy) * g.px;
+    float m[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cx = lane + 32 * j, gx = x0 + cx;
-        const int c = (row + r) * kGenW + cx + kHaloX;
-        float acc = 0.f;
-        for (int k = 0; k < npts; ++k) acc = __fmaf_rn(s_w[k], ring[s_koff[k] + c], acc);
-        float v = 0.f;
-        if (gy < g.ny && gx < g.nx) {
-          v = __fadd_rn(__ldg(Crow + (size_t)gy * g.px + gx), acc);
-          for (int f = 0; f < nf; ++f)
-            if (lf[f].x == gx && lf[f].y == gy && lf[f].z == z) v = __int_as_float(__float_as_int(v) ^ (1 << lf[f].w));
-          Urow[(size_t)gy * g.px + gx] = v;
-        }
-        m[j] = v;
-        if (PROT) col_add<ACC>(ca[j], v);
+    for (int j = 0; j < 4; ++j) {
+      const int gx = x0 + lane + 32 * j;
+      float v = 0.f;
+      if (gy < g.ny && gx < g.nx) {
+        v = __fadd_rn(cs[32 * j], acc[j]);
+        for (int f = 0; f < nf; ++f)
+          if (lf[f].x == gx && lf[f].y == gy && lf[f].z == z) v = __int_as_float(__float_as_int(v) ^ (1 << lf[f].w));
+        Urow[gx] = v;
       }
+      m[j] = v;
       if (PROT) {
-        T t = RP::of(m);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t = RP::comb(t, RP::shfl(t, o));
-        if (lane == 0 && gy < g.ny) RP::store(g.PB, ((size_t)txi * g.nz + z) * g.pb_stride + gy, t);
+        ca[j] = col_zero<ACC>();
+        col_add<ACC>(ca[j], v);
       }
+    }
+    if (PROT) {
+      T t = RP::of(m);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t = RP::comb(t, RP::shfl(t, o));
+      if (lane == 0 && gy < g.ny) RP::store(g.PB, ((size_t)txi * g.nz + z) * g.pb_stride + gy, t);
     }
     __syncthreads();  // the slot of plane z - r and the column scratch are free again
     if (PROT) {
@@ -350,8 +383,8 @@ __global__ void __launch_bounds__(256)
 // ------------------------------------------------------------ launchers
 
 int gen_sweep_smem(const GridDev& g, int r) {
-  const int R = g.ty + 2 * r, S = 2 * r + 2;
-  return S * R * kGenW * (int)sizeof(float) + 8 * kTX * (g.acc == ABFT_ACC_FP32 ? 4 : 8);
+  const int S = 2 * r + 1 + kGenAhead;
+  return S * gen_slot_floats(r) * (int)sizeof(float) + 8 * kTX * (g.acc == ABFT_ACC_FP32 ? 4 : 8);
 }
 
 template <int ACC, bool PROT>
@@ -364,7 +397,7 @@ static cudaError_t sweep_gen_as(const Launch& L, const GridDev& g, int r, int in
 }
 
 cudaError_t launch_sweep_gen(const Launch& L, const GridDev& g, int r, int in, int out, bool prot) {
-  if (r < 0 || r > kGenRadius || g.ty % 8 != 0) return cudaErrorInvalidValue;
+  if (r < 0 || r > kGenRadius || g.ty != kGenTY) return cudaErrorInvalidValue;
   if (!prot) return sweep_gen_as<ABFT_ACC_FP32, false>(L, g, r, in, out);
   switch (g.acc) {
     case ABFT_ACC_TWOSUM: return sweep_gen_as<ABFT_ACC_TWOSUM, true>(L, g, r, in, out);

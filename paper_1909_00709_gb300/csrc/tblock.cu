@@ -14,8 +14,18 @@
 // Every level uses the point update of the single-sweep kernel (hs_update, the same
 // clamps at the grid's faces) and applies the flips scheduled for its sweep to every
 // point it computes, halo included, so the result is bit-identical to K single
-// sweeps.  The kernel writes no checksum partials: the protected sweeps (online, and
-// the last sweep of an offline window) stay single sweeps.
+// sweeps.
+//
+// Protected passes (online checks with temporal blocking, PVEC = 1 or 2) also write the
+// partial checksums of every level over the CTA's own 128 x TY region: the b partial of
+// each row (the lane sums of four values and the warp butterfly of the single-sweep
+// epilogue, so the b checksums equal a single sweep's bit for bit) and, with PVEC = 2,
+// the a partial of each column (its TY values in row order).  A check of all K levels
+// then runs after the pass (k_check_tb_level); a level that fails sends the pass back to
+// single sweeps from its input (the pass never overwrites it).
+#include <algorithm>
+
+#include "check_dev.cuh"
 #include "sweep_tile.cuh"
 
 namespace abft {
@@ -58,11 +68,13 @@ __device__ __forceinline__ void tb_update4(const Coef& k, float4 c, float4 n, fl
   v[3] = hs_update(k, c.w, c.z, e3, n.w, s.w, b.w, t.w, cs.w);
 }
 
-template <int TY, int K>
+template <int TY, int K, int PVEC>
 __global__ void __launch_bounds__(256, TbCfg<TY, K>::MIN_BLOCKS)
     k_sweep_tb(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_c, const GridDev g,
-               float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched) {
+               float* __restrict__ uout, DevCtrl* __restrict__ ctrl, DevSched sched, TbLevels lp) {
   using Cfg = TbCfg<TY, K>;
+  static_assert(TY == Cfg::NW, "protected passes reduce one owned row per warp");
+  __shared__ float colk[PVEC == 2 ? Cfg::NW * kTX : 1];  // level K values of the owned rows (a partials)
   constexpr int S = Cfg::S, R = Cfg::R, NW = Cfg::NW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* sb = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -183,6 +195,16 @@ __global__ void __launch_bounds__(256, TbCfg<TY, K>::MIN_BLOCKS)
             float v[4];
             tb_update4(g.k, c, n, s, b, t, wl, er, cs, gx, nx, v);
             if (nflip > 0) flip4(v, K, p, gy, gx);
+            if (PVEC) {  // level K's partials: the row's b partial now, the columns after the barrier
+              float m[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) m[e] = (gy < ny && gx + e < nx) ? v[e] : 0.f;
+              const float rsum = warp_sum(((m[0] + m[1]) + m[2]) + m[3]);
+              if (lane == 0 && gy < ny) static_cast<float*>(lp.PB[K - 1])[((size_t)txi * nz + p) * g.pb_stride + gy] = rsum;
+              if (PVEC == 2)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) colk[warp * kTX + 4 * lane + e] = m[e];
+            }
             if (gy < ny && gx < nx) {
               float* out = uout + ((size_t)p * ny + gy) * g.px + gx;
               const int last = nx - 1 - gx;
@@ -198,6 +220,31 @@ __global__ void __launch_bounds__(256, TbCfg<TY, K>::MIN_BLOCKS)
         }
       }
       __syncthreads();
+    }
+    if (PVEC) {  // partials of the owned region at every level computed in this iteration
+#pragma unroll
+      for (int tau = 1; tau < K; ++tau) {
+        const int p = i - tau;
+        if (p < 0 || p >= nz) continue;
+        const float* L = lv(tau, p);
+        const int gy = y0 + warp, gx = x0 + 4 * lane;  // owned row `warp`, columns of this lane
+        const float4 c = *reinterpret_cast<const float4*>(L + (K + warp) * kUW + kHaloX + 4 * lane);
+        const float m[4] = {(gy < ny && gx < nx) ? c.x : 0.f, (gy < ny && gx + 1 < nx) ? c.y : 0.f,
+                            (gy < ny && gx + 2 < nx) ? c.z : 0.f, (gy < ny && gx + 3 < nx) ? c.w : 0.f};
+        const float rsum = warp_sum(((m[0] + m[1]) + m[2]) + m[3]);
+        if (lane == 0 && gy < ny) static_cast<float*>(lp.PB[tau - 1])[((size_t)txi * nz + p) * g.pb_stride + gy] = rsum;
+        if (PVEC == 2 && tid < kTX && x0 + tid < nx) {
+          float a = 0.f;
+          for (int rr = 0; rr < TY && y0 + rr < ny; ++rr) a += L[(K + rr) * kUW + kHaloX + tid];
+          static_cast<float*>(lp.PA[tau - 1])[((size_t)tyi * nz + p) * g.pa_stride + x0 + tid] = a;
+        }
+      }
+      const int pk = i - K;
+      if (PVEC == 2 && pk >= 0 && pk < nz && tid < kTX && x0 + tid < nx) {
+        float a = 0.f;
+        for (int rr = 0; rr < TY && y0 + rr < ny; ++rr) a += colk[rr * kTX + tid];
+        static_cast<float*>(lp.PA[K - 1])[((size_t)tyi * nz + pk) * g.pa_stride + x0 + tid] = a;
+      }
     }
     // plane i-K's stage (its C was read by level K just now) takes plane i-K+S
     if (tid == 0 && i - K >= 0 && i - K + S < nz) {
@@ -221,26 +268,78 @@ __global__ void __launch_bounds__(256, TbCfg<TY, K>::MIN_BLOCKS)
 
 constexpr int kTbTY = kTbRows;
 
-template <int K>
+template <int K, int PVEC>
 static cudaError_t tb_launch(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
-                             float* uout) {
-  auto kern = k_sweep_tb<kTbTY, K>;
+                             float* uout, const TbLevels& lp) {
+  auto kern = k_sweep_tb<kTbTY, K, PVEC>;
   const int smem = TbCfg<kTbTY, K>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int blocks = g.ntx * ((g.ny + kTbTY - 1) / kTbTY);
-  kern<<<blocks, 256, smem, L.s>>>(tm_in, tm_c, g, uout, L.ctrl, L.sched);
+  kern<<<blocks, 256, smem, L.s>>>(tm_in, tm_c, g, uout, L.ctrl, L.sched, lp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_tb(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
                             int out, int k) {
+  const TbLevels none{};
   switch (k) {
-    case 2: return tb_launch<2>(L, g, tm_in, tm_c, g.u[out]);
-    case 3: return tb_launch<3>(L, g, tm_in, tm_c, g.u[out]);
-    case 4: return tb_launch<4>(L, g, tm_in, tm_c, g.u[out]);
+    case 2: return tb_launch<2, 0>(L, g, tm_in, tm_c, g.u[out], none);
+    case 3: return tb_launch<3, 0>(L, g, tm_in, tm_c, g.u[out], none);
+    case 4: return tb_launch<4, 0>(L, g, tm_in, tm_c, g.u[out], none);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_sweep_tb_prot(const Launch& L, const GridDev& g, const CUtensorMap& tm_in, const CUtensorMap& tm_c,
+                                 int out, int k, const TbLevels& lp) {
+  const bool two = g.vec == 2;
+  switch (k) {
+    case 2: return two ? tb_launch<2, 2>(L, g, tm_in, tm_c, g.u[out], lp) : tb_launch<2, 1>(L, g, tm_in, tm_c, g.u[out], lp);
+    case 3: return two ? tb_launch<3, 2>(L, g, tm_in, tm_c, g.u[out], lp) : tb_launch<3, 1>(L, g, tm_in, tm_c, g.u[out], lp);
+    case 4: return two ? tb_launch<4, 2>(L, g, tm_in, tm_c, g.u[out], lp) : tb_launch<4, 1>(L, g, tm_in, tm_c, g.u[out], lp);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------------ level checks
+
+// The check of level tau of a protected pass (Sec. 3, one level after the other): the
+// level's partials (gt.PA/gt.PB, tiles of kTbRows rows) reduced in the canonical
+// order into (a_out, b_out), Theorem 1 from the level before (a_prev, b_prev; the
+// boundary terms vanish for the grids temporal blocking serves), the Sec. 3.4 test;
+// failing entries are only counted (gt.gc->verdict): a failing pass is recomputed.
+__global__ void __launch_bounds__(256)
+    k_check_tb_level(const GridDev gt, const double* a_prev, const double* b_prev, double* a_out, double* b_out) {
+  const int na = gt.vec == 2 ? gt.nz * gt.nx : 0, n = na + gt.nz * gt.ny;
+  unsigned long long nf = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < na) {
+      const int z = i / gt.nx, x = i - z * gt.nx;
+      const double s = reduce_a<ABFT_ACC_FP32>(gt, z, x);
+      a_out[i] = s;
+      const double p = predict_a(gt, a_prev, nullptr, z, x);
+      if (fails(p, s, gt.eps)) ++nf;
+      note_resid(gt, p, s);
+    } else {
+      const int j = i - na;
+      const int z = j / gt.ny, y = j - z * gt.ny;
+      const double s = reduce_b<ABFT_ACC_FP32>(gt, z, y);
+      b_out[j] = s;
+      const double p = predict_b(gt, b_prev, nullptr, z, y);
+      if (fails(p, s, gt.eps)) ++nf;
+      note_resid(gt, p, s);
+    }
+  }
+  if (nf) atomicAdd(&gt.gc->verdict, nf);
+}
+
+cudaError_t launch_check_tb_level(const Launch& L, const GridDev& gt, const double* a_prev, const double* b_prev,
+                                  double* a_out, double* b_out) {
+  const long long n = (long long)gt.nz * ((gt.vec == 2 ? gt.nx : 0) + gt.ny);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8 * 152));
+  k_check_tb_level<<<blocks, 256, 0, L.s>>>(gt, a_prev, b_prev, a_out, b_out);
+  return cudaGetLastError();
 }
 
 }  // namespace abft

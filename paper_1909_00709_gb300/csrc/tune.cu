@@ -50,7 +50,7 @@ std::string key_of(const abft_grid* g, int n, const abft_options* o, int mode, i
 
 // the settings a candidate actually changes for these grids (so equivalent candidates
 // are timed once): per grid the tile class, then persistence, batching and depth
-std::string effect_of(const abft_grid* g, int n, const Cand& c, int mode, int bc) {
+std::string effect_of(const abft_grid* g, int n, const Cand& c, int mode, int bc, int acc) {
   std::string e;
   char b[32];
   for (int i = 0; i < n; ++i) {
@@ -60,13 +60,13 @@ std::string effect_of(const abft_grid* g, int n, const Cand& c, int mode, int bc
     e += b;
   }
   snprintf(b, sizeof b, "p%db%dd%d", n > 1 && c.batch ? 0 : c.persistent, n > 1 ? c.batch : 0,
-           mode == ABFT_MODE_ONLINE || bc != ABFT_BC_CLAMP ? 1 : c.depth);
+           bc != ABFT_BC_CLAMP || (mode == ABFT_MODE_ONLINE && (n > 1 || acc != ABFT_ACC_FP32)) ? 1 : c.depth);
   return e + b;
 }
 
-// temporal depth only matters for the unprotected sweeps (mode NONE, offline windows)
-// of clamped grids
-std::vector<Cand> candidates(const abft_grid* g, int n, int mode, int bc) {
+// temporal depth matters for clamped grids: unprotected sweeps (mode NONE, offline
+// windows) and online checks of a single grid with FP32 checksums
+std::vector<Cand> candidates(const abft_grid* g, int n, int mode, int bc, int acc) {
   std::vector<Cand> out;
   std::vector<std::string> seen;
   for (int depth : {1, 2, 3, 4})
@@ -75,7 +75,7 @@ std::vector<Cand> candidates(const abft_grid* g, int n, int mode, int bc) {
         for (int shallow : {1, 0})
           for (int ty : {8, 16, 32}) {
             const Cand c{ty, shallow, persistent, batch, depth};
-            const std::string e = effect_of(g, n, c, mode, bc);
+            const std::string e = effect_of(g, n, c, mode, bc, acc);
             if (std::find(seen.begin(), seen.end(), e) != seen.end()) continue;
             seen.push_back(e);
             out.push_back(c);
@@ -99,7 +99,7 @@ extern "C" ABFT_API size_t abft_tune_workspace_bytes(const abft_grid* grids, int
                                                      const abft_options* base) {
   if (!grids || n_grids < 1 || !base) return 0;
   size_t m = 0;
-  for (const Cand& c : candidates(grids, n_grids, ABFT_MODE_NONE, base->boundary)) {
+  for (const Cand& c : candidates(grids, n_grids, ABFT_MODE_NONE, base->boundary, base->acc)) {
     const abft_options o = with(*base, c);
     const size_t b = abft_workspace_bytes(grids, n_grids, &o);
     if (b == 0) return 0;
@@ -134,7 +134,7 @@ extern "C" ABFT_API abft_status abft_tune(const abft_grid* grids, int32_t n_grid
   double best_us = -1.0;
   abft_options win = *base;
   abft_status st = ABFT_OK;
-  for (const Cand& c : candidates(grids, n_grids, mode, base->boundary)) {
+  for (const Cand& c : candidates(grids, n_grids, mode, base->boundary, base->acc)) {
     const abft_options o = with(*base, c);
     const size_t need = abft_workspace_bytes(grids, n_grids, &o);
     if (need == 0 || need > workspace_bytes) continue;
