@@ -45,7 +45,7 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) per sweep of the dominant kernel, from one ncu capture of
 # the current build (the working set stays in L2); None for kernels not captured since
 # they last changed
-TRAFFIC_PER_SWEEP = {"k_persist_online": None}
+TRAFFIC_PER_SWEEP = {"k_persist_online": (16932608 + 97280) / 1000}  # one 1000-sweep launch, 512x512x8
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
@@ -555,8 +555,13 @@ def side_runs(dev, stream, flush, hbm_peak):
     import torch
     from paper_1909_00709_gb300 import abi, inputs
 
+    cache = {}  # the seeded inputs of each (shape, seed), generated once and kept on the device
+
     def timed(shape, mode, sweeps, seed, inject=0.0, **opt):
-        t, p = inputs.grid_inputs(*shape, seed=seed)
+        if (shape, seed) not in cache:
+            t_, p_ = inputs.grid_inputs(*shape, seed=seed)
+            cache[(shape, seed)] = (torch.from_numpy(t_).to(dev), torch.from_numpy(p_).to(dev))
+        t, p = cache[(shape, seed)]
         with abi.Context([shape], [t], [p], [inputs.hotspot_coeffs(*shape)], device=dev, stream=stream,
                          **opt) as c:
             if inject:
@@ -627,6 +632,36 @@ def side_runs(dev, stream, flush, hbm_peak):
                                **tuned_large[key], **extra)
     for name, mode in (("unprotected_default_options", abi.MODE_NONE), ("offline_default_options", abi.MODE_OFFLINE)):
         large[name], _ = timed(LARGE_SHAPE, mode, LARGE_SWEEPS, 4, max_flips_per_step=511)
+    # temporal blocking (Sec. 4's offline windows and the online check in passes of
+    # `depth` sweeps, every level checked): fault-free and with one flip per sweep, on an
+    # HBM-bound 512x512x64 grid and the 1024x1024x256 one, launched sweep by sweep
+    tb = {}
+    for shape, sweeps in ((PRECISION_SHAPE, 200), (LARGE_SHAPE, 40)):
+        r = {}
+        for d in (1, 2, 3):
+            r[f"unprotected_depth{d}"] = timed(shape, abi.MODE_NONE, sweeps, 4, persistent=0, depth=d)[0]
+            r[f"offline_depth{d}"] = timed(shape, abi.MODE_OFFLINE, sweeps, 4, persistent=0, depth=d)[0]
+            r[f"online_1_vector_depth{d}"] = timed(shape, abi.MODE_ONLINE, sweeps, 4, persistent=0, overlap=0,
+                                                   vectors=1, depth=d)[0]
+        for d in (1, 2):
+            r[f"online_1_vector_depth{d}_1_flip_per_sweep"] = timed(shape, abi.MODE_ONLINE, sweeps, 4, inject=1.0,
+                                                                     persistent=0, overlap=0, vectors=1, depth=d)[0]
+        tb["x".join(map(str, shape))] = r
+    # general stencil sets (Sec. 3.1) and the constant boundary (Sec. 3.3) through the
+    # general kernels, 1024x1024x64
+    gshape = (1024, 1024, 64)
+    star = [(0, 0, 0, 0.5)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
+           [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)]
+    box = [(i, j, k, 1.0 / 27) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1)]
+    gen = {}
+    for gname, kw in (("star13_clamped", dict(stencils=[star])), ("box27_clamped", dict(stencils=[box])),
+                      ("star13_constant", dict(stencils=[star], boundary=abi.BC_CONST, boundary_value=318.15)),
+                      ("hotspot7_constant", dict(boundary=abi.BC_CONST, boundary_value=318.15))):
+        r = {}
+        for mname, mode in (("unprotected", abi.MODE_NONE), ("online", abi.MODE_ONLINE), ("offline", abi.MODE_OFFLINE)):
+            r[mname] = timed(gshape, mode, 40, 4, **kw)[0]
+        r["online_1_flip_per_sweep"] = timed(gshape, abi.MODE_ONLINE, 40, 4, inject=1.0, **kw)[0]
+        gen[gname] = r
     # many uneven grids: batched launches (one sweep launch per tile class, one check
     # launch per sweep, graphs of 50 sweeps, tiles autotuned; the unprotected run uses the
     # same options) against the same grids advanced one by one
@@ -721,7 +756,13 @@ def side_runs(dev, stream, flush, hbm_peak):
         errs = np.array(errs)
         errcamp[name] = {"median_l2": float(np.median(errs)), "mean_l2": float(np.mean(errs[np.isfinite(errs)])),
                          "share_exact": float(np.mean(errs == 0.0))}
-    return {"boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16},
+    return {"temporal_blocking": {"glups": tb, "note": "launched sweep by sweep (persistent=0); online: one "
+                                  "checksum vector, passes of `depth` sweeps, every level checked, a failed pass "
+                                  "recomputed sweep by sweep"},
+            "general_stencils": {"shape": list(gshape), "sweeps": 40, "glups": gen,
+                                 "sets": {"star13": "centre 1/2, x and y offsets +-1, +-2 at 1/16",
+                                          "box27": "27-point box, 1/27 each"}},
+            "boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16},
             "one_vector": {"glups": onev, "mode": "online; *_flips at the stated rate"}, "batch": batch,
             "bit_campaign": campaign, "offline_period_sweep": dsweep, "error_campaign": errcamp,
             "large": {"shape": list(LARGE_SHAPE), "sweeps": LARGE_SWEEPS,
