@@ -1145,7 +1145,8 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
         continue;
       }
       for (int gi : which) {
-        const GridDev& g = ctx->g[gi];
+        GridDev g = ctx->g[gi];
+        g.vec = 2;  // a window's last sweep forms both vectors whatever the online option
         const int in = ctx->cur[gi], out = other_than(in, ctx->ref[gi]);
         const bool last = k == d - 1;
         if (!simple_chain(ctx, gi)) {  // link k of the chain, with the terms of this sweep's input
@@ -1165,7 +1166,8 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
       }
     }
     for (int gi : which) {
-      const GridDev& g = ctx->g[gi];
+      GridDev g = ctx->g[gi];
+      g.vec = 2;
       const int c = ctx->cur[gi];
       CK(run(ctx, kKCheckOffline, [&] { return launch_reduce_partials(L, g, c); }));
       const int slot = (int)((d - 1) & 1);
@@ -1603,7 +1605,8 @@ abft_status abft_verify(abft_ctx* ctx, int64_t* n_mismatch) {
   if (s) return s;
   ctx->v_dist.assign(ctx->n, 0);
   for (int gi = 0; gi < ctx->n; ++gi) {
-    const GridDev& g = ctx->g[gi];
+    GridDev g = ctx->g[gi];
+    g.vec = 2;  // verification compares both vectors whatever the online option
     const int c = ctx->cur[gi], r = ctx->ref[gi];
     const int64_t d = ctx->step - ctx->ref_step[gi];
     ctx->v_dist[gi] = d;

@@ -209,3 +209,30 @@ def test_compensated_and_fp64_accumulation(abi, orc, acc, persistent):
     g, o = compare_events(ev, ref)
     assert g == o and len(o) >= 4
     assert rel_err(got, ref["u"]) < 1e-5
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_offline_windows_in_a_one_vector_context(abi, orc, persistent):
+    """Offline windows form both checksum vectors whatever the online option: launched
+    window by window (and by the persistent kernel) in a context created with one vector,
+    after online sweeps, with a flip to roll back; events and values against the oracle."""
+    shape = (200, 37, 5)
+    fl = inputs.flip_list([(6, 0, 2, 10, 30, 29), (21, 0, 1, 20, 150, 27)])
+    with gpu_context(abi, [shape], [4], vectors=1, persistent=persistent) as ctx:
+        ctx.inject_list(fl)
+        ctx.step(8, ONLINE)
+        ctx.step(32, OFFLINE)
+        got = ctx.read(0)
+        ev = ctx.events()
+        rb = ctx.counters()["rollbacks"]
+    ref_on = oracle_run(orc, shape, 4, 8, orc.MODE_ONLINE, fl, vectors=1)
+    co = inputs.hotspot_coeffs(*shape)
+    _, power = inputs.grid_inputs(*shape, seed=4)
+    st = orc.Stencil(shape, orc.hotspot_points(co))
+    ref = orc.run(st, orc.source_term(power, co), ref_on["u"], 32, orc.MODE_OFFLINE, fl, t0=8)
+    assert rb == ref["n_rollbacks"] == 1
+    g = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"])) for e in ev}
+    o = {(int(e["step"]), int(e["z"]), int(e["y"]), int(e["x"]), int(e["kind"]))
+         for e in list(ref_on["events"]) + list(ref["events"])}
+    assert g == o
+    assert rel_err(got, ref["u"]) < 1e-5
