@@ -1099,9 +1099,11 @@ abft_status clear_verdicts(abft_ctx* ctx) {
 }
 
 // chain Theorem 1 d times from (a0, b0); returns the index of the AP/BP slot holding the result
-abft_status chain(abft_ctx* ctx, int gi, const double* a0, const double* b0, int64_t d, int* slot) {
+abft_status chain(abft_ctx* ctx, int gi, const double* a0, const double* b0, int64_t d, int* slot,
+                  cudaStream_t on = nullptr) {
   const GridDev& g = ctx->g[gi];
-  const Launch L = launcher(ctx);
+  Launch L = launcher(ctx);
+  if (on) L.s = on;
   const double* a = a0;
   const double* b = b0;
   int s = 0;
@@ -1127,6 +1129,17 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   }
   abft_status s = clear_verdicts(ctx);
   if (s) return s;
+  // The chains of Fig. 10 that need no grid (Eq. 6/7) depend only on the checkpoint's
+  // checksums: they run on a side stream beside the window's sweeps and join before the
+  // comparison (not while kernels are being timed one by one).
+  bool side = !ctx->timing, forked = false, joined = false;
+  if (side) {
+    cudaError_t e = cudaSuccess;
+    if (!ctx->side_stream) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->fork_ev) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->join_ev) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(ctx, ABFT_E_CUDA, "offline set-up: %s", cudaGetErrorString(e));
+  }
   auto run_window = [&](const std::vector<int>& which) -> abft_status {
     bool all_simple = true;  // per-step chains need every intermediate state
     for (int gi : which) all_simple = all_simple && simple_chain(ctx, gi);
@@ -1165,6 +1178,10 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
         ctx->cur[gi] = out;
       }
     }
+    if (side && !joined) {  // the chains ran beside the window's sweeps
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+      joined = true;
+    }
     for (int gi : which) {
       GridDev g = ctx->g[gi];
       g.vec = 2;
@@ -1179,10 +1196,18 @@ abft_status offline_window(abft_ctx* ctx, int64_t d) {
   for (int gi = 0; gi < ctx->n; ++gi) {
     all[gi] = gi;
     if (!simple_chain(ctx, gi)) continue;  // chained sweep by sweep inside the window
+    if (side && !forked) {
+      CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+      CK(cudaStreamWaitEvent(ctx->side_stream, ctx->fork_ev, 0));
+      forked = true;
+    }
     int slot;
-    s = chain(ctx, gi, ctx->g[gi].A[ctx->ref[gi]], ctx->g[gi].B[ctx->ref[gi]], d, &slot);
+    s = chain(ctx, gi, ctx->g[gi].A[ctx->ref[gi]], ctx->g[gi].B[ctx->ref[gi]], d, &slot,
+              side ? ctx->side_stream : nullptr);
     if (s) return s;
   }
+  if (forked) CK(cudaEventRecord(ctx->join_ev, ctx->side_stream));
+  else side = false;
   s = run_window(all);
   if (s) return s;
   s = read_ctrl(ctx);
