@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_batch(const BatchArgs a, DevCt
 // partials per round and warp; otherwise plain coalesced loads); that grid's last
 // block to finish locates and corrects (Sec. 3.5).
 template <int ACC, bool BOX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_check_batch(const BatchArgs a, int box, DevCtrl* __restrict__ ctrl, abft_event* __restrict__ ev) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int slot = batch_slot(a.off, a.n, blockIdx.x);

@@ -597,6 +597,17 @@ __device__ __forceinline__ void check_lane(const GridDev& g, const InterpW& w, i
   using T = typename PartialType<ACC>::T;
   LaneSum L[kLanes];
   int q = 0;
+  // partials fetched kDeep lane steps at a time, so that many loads are in flight (an a
+  // entry sums one partial per tile row); each lane sum still takes its partials in
+  // ascending order
+  constexpr int kDeep = sizeof(T) == 4 ? 4 : 2;
+  for (; q + kDeep * kLanes <= np; q += kDeep * kLanes) {
+    T v[kDeep * kLanes];
+#pragma unroll
+    for (int j = 0; j < kDeep * kLanes; ++j) v[j] = load_raw<ACC>(P, i0 + (size_t)(q + j) * stride);
+#pragma unroll
+    for (int j = 0; j < kDeep * kLanes; ++j) L[j % kLanes].add(v[j]);
+  }
   for (; q + kLanes <= np; q += kLanes) {
     T v[kLanes];
 #pragma unroll
