@@ -736,7 +736,7 @@ abft_status online_overlap(abft_ctx* ctx, int64_t n) {
 
 // Work lists of the batched launches: grids grouped by tile class, deepest first;
 // the check launch gives each grid blocks of 32-entry rounds (eight per warp with TMA
-// boxes, kBatchRounds per block otherwise).
+// boxes; otherwise kBatchMinRounds to kBatchRounds per block, by the batch's size).
 void build_batch_tables(abft_ctx* ctx) {
   const int n = ctx->n;
   ctx->h_btmap.resize((size_t)kBatchMaps * n);
@@ -794,14 +794,24 @@ void build_batch_tables(abft_ctx* ctx) {
   k.box = box ? box_bytes : 0;
   k.nw = box ? check_box_warps(box_bytes) : 8;
   k.smem = box ? 256 + k.nw * box_bytes : 0;
-  const int per_block = box ? 8 * k.nw : kBatchRounds;  // 32-entry rounds per block
+  auto rounds_of = [&](const GridDev& g) -> int64_t {
+    return box ? check_rounds_host(g) : ((int64_t)g.nz * (g.nx + g.ny) - check_entries_first(g) + 31) / 32;
+  };
+  // 32-entry rounds per block: with plain loads, as many as keep about four waves of two
+  // blocks per SM (a block's set-up is spread over its rounds), between kBatchMinRounds
+  // and kBatchRounds
+  int per_block = 8 * k.nw;
+  if (!box) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev) != cudaSuccess || sms < 1) sms = 1;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) total += rounds_of(ctx->g[i]);
+    per_block = (int)std::min<int64_t>(kBatchRounds, std::max<int64_t>(kBatchMinRounds, total / (8LL * sms)));
+  }
   std::vector<int> koff{0};
   for (int i = 0; i < n; ++i) {
-    const GridDev& g = ctx->g[i];
     grids.push_back(i);
-    const int64_t rounds = box ? check_rounds_host(g)
-                               : ((int64_t)g.nz * (g.nx + g.ny) - check_entries_first(g) + 31) / 32;
-    koff.push_back(koff.back() + (int)((rounds + per_block - 1) / per_block));
+    koff.push_back(koff.back() + (int)((rounds_of(ctx->g[i]) + per_block - 1) / per_block));
   }
   k.n = n;
   k.blocks = koff.back();

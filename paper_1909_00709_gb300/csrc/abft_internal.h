@@ -244,7 +244,8 @@ struct BatchArgs {
   const int* off;            // [n + 1]
   int n;
 };
-constexpr int kBatchRounds = 16;  // 32-entry check rounds per block of the batched check (2 per warp)
+constexpr int kBatchRounds = 128;    // most 32-entry check rounds per block of the batched check (16 per warp)
+constexpr int kBatchMinRounds = 16;  // fewest (2 per warp)
 int batch_sweep_smem(int shallow, int ty, int nz);
 // bc: the grids' abft_boundary (one rule per context)
 cudaError_t batch_prepare(int shallow, int ty, bool prot, int acc, int bc, int smem);
