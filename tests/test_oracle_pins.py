@@ -560,3 +560,31 @@ def test_one_vector_square_grid_under_other_boundaries(orc, boundary):
                            for e in r["events"])
     assert key(both) == key(one) and len(key(one)) == 4
     assert all(k[4] == orc.EV_CORRECTED for k in key(one))
+
+
+@pytest.mark.parametrize("bit", [14, 18, 22])  # mantissa bits: residual well below eps = 1
+def test_guard_band_logs_flips_near_the_threshold(orc, bit):
+    """Sec. 3.4's test compares |a' - a| / |a| with eps; the oracle logs, as marginal, the
+    (sweep, plane) pairs whose ratio to eps falls within 5 % of 1.  A flip's own residual r
+    (the largest of the run when nothing is caught, eps = 1) placed just inside the band on
+    either side of the threshold is logged -- caught at eps = r / 1.03, missed at 1.03 r --
+    and placed well outside it (r / 3 caught, 3 r missed) is not."""
+    st, C, temp = hotspot(orc, (64, 64, 8), 4)
+    z = 3
+    fl = inputs.flip_list([(6, 0, z, 20, 30, bit)])
+    free = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, eps=1.0)
+    assert free["n_events"] == 0 and not free["marginal"]
+    r = free["max_resid"]
+    assert r > 1e-9  # far above the FP64 residual of a fault-free sweep
+    caught = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, eps=r / 1.03)
+    assert caught["n_events"] >= 1
+    steps = {int(e["step"]) for e in caught["events"]}
+    assert {int(e["z"]) for e in caught["events"]} == {z} and len(steps) == 1
+    assert caught["marginal"] == {(steps.pop(), z)}
+    missed = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, eps=r * 1.03)
+    assert missed["n_events"] == 0
+    assert missed["marginal"] == caught["marginal"]
+    clear_hit = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, eps=r / 3)
+    assert clear_hit["n_events"] >= 1 and not clear_hit["marginal"]
+    clear_miss = orc.run(st, C, temp, 12, orc.MODE_ONLINE, fl, eps=r * 3)
+    assert clear_miss["n_events"] == 0 and not clear_miss["marginal"]
