@@ -698,6 +698,39 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
   tile_sync();
 }
 
+// Periodic boundaries on whole-column tiles: the wrapped values of the rows of plane z
+// that this lane needs -- u at x = nx - 1 for a row's first point (W[r]), at x = 0 for
+// its last (W[TY + r]), and on a y face the row on the other face (W + 2 TY: for y = 0;
+// W + 2 TY + kTX: for y = ny - 1) -- copied from global memory to the plane's slice W of
+// a shared buffer.  Called before the wait for the tile's copy, so that these loads run
+// while it is in flight; a lane later reads only what it wrote.
+template <int TY>
+__device__ __forceinline__ void wrap_fetch(const GridDev& g, const float* __restrict__ uin, int z, int y0, int gx0,
+                                           int last, int lane, float* W) {
+  if (last < 0) return;  // no grid point among the lane's four
+  float xw[TY], xe[TY];
+  float4 yn = make_float4(0.f, 0.f, 0.f, 0.f), ys = yn;
+  const float* base = uin + (size_t)z * g.ny * g.px;
+#pragma unroll
+  for (int r = 0; r < TY; ++r) {
+    const int y = y0 + r;
+    xw[r] = xe[r] = 0.f;
+    if (y >= g.ny) continue;
+    const float* row = base + (size_t)y * g.px;
+    if (gx0 == 0) xw[r] = __ldcg(row + g.nx - 1);
+    if (last <= 3) xe[r] = __ldcg(row);
+    if (y == 0) yn = __ldcg(reinterpret_cast<const float4*>(base + (size_t)(g.ny - 1) * g.px + gx0));
+    else if (y == g.ny - 1) ys = __ldcg(reinterpret_cast<const float4*>(base + gx0));
+  }
+#pragma unroll
+  for (int r = 0; r < TY; ++r) {
+    if (gx0 == 0) W[r] = xw[r];
+    if (last <= 3) W[TY + r] = xe[r];
+  }
+  if (y0 == 0) *reinterpret_cast<float4*>(W + 2 * TY + 4 * lane) = yn;
+  if (y0 + TY >= g.ny) *reinterpret_cast<float4*>(W + 2 * TY + kTX + 4 * lane) = ys;
+}
+
 template <int TY, bool PROT, int ACC, int BC, int VEC = 2>
 __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* __restrict__ uin,
                                                  float* __restrict__ uout, int txi, int tyi,
@@ -707,22 +740,29 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = txi * kTX, y0 = tyi * TY;
   const int nz = g.nz;
+  const int gx0 = x0 + 4 * lane;
+  const int last = g.nx - 1 - gx0;
+  // periodic: this warp's planes' wrapped values, fetched while the tile's copy is in flight
+  constexpr bool WRAP = BC == ABFT_BC_PERIODIC;
+  constexpr int WPL = 2 * TY + 2 * kTX;  // floats of wrapped values per plane
+  __shared__ __align__(16) float wbuf[WRAP ? kShallowMaxZ * WPL : 4];
+  if (WRAP)
+    for (int z = warp; z < nz; z += NW) wrap_fetch<TY>(g, uin, z, y0, gx0, last, lane, wbuf + z * WPL);
   mbar_wait(sm.bar, phase, ctrl);
   phase ^= 1u;
+  if (WRAP) __syncwarp();
   const int nflip = min(*sm.nlf, kLocalFlips);
   void* PA = pbuf ? g.PA2 : g.PA;
   void* PB = pbuf ? g.PB2 : g.PB;
-  const int gx0 = x0 + 4 * lane;
-  const int last = g.nx - 1 - gx0;
   const bool full = x0 + kTX <= g.nx && y0 + TY <= g.ny;  // no ragged edge in this tile
   constexpr int PLANE = (TY + 2) * kUW;
   constexpr bool PA_ON = PROT && VEC == 2;  // column partials (the a vector)
   for (int z = warp; z < nz; z += NW) {
     const float* Uz = sm.u + z * PLANE;
     // at a z face: the centre plane, or for periodic boundaries the staged opposite face
-    constexpr bool wrap = BC == ABFT_BC_PERIODIC;
-    const float* Ub = z > 0 ? Uz - PLANE : (wrap ? Uz + (nz - 1) * PLANE : Uz);
-    const float* Ut = z + 1 < nz ? Uz + PLANE : (wrap ? sm.u : Uz);
+    const float* Ub = z > 0 ? Uz - PLANE : (WRAP ? Uz + (nz - 1) * PLANE : Uz);
+    const float* Ut = z + 1 < nz ? Uz + PLANE : (WRAP ? sm.u : Uz);
+    const float* W = wbuf + (WRAP ? z * WPL : 0);
     const float* Cz = sm.c + z * TY * kTX;
     AccA<ACC> acc;
     if (PA_ON) acc.zero();
@@ -743,7 +783,14 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
       if (lane == 31) er = Uz[o + 4];
       float w0 = wl;
       float e0 = c.y, e1 = c.z, e2 = c.w, e3 = er;
-      boundary_cells<true, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3);
+      WrapRow pre{0.f, 0.f, make_float4(0.f, 0.f, 0.f, 0.f)};
+      if (WRAP && y < g.ny && last >= 0) {
+        pre.xw = W[r];
+        pre.xe = W[TY + r];
+        if (y == 0) pre.yf = *reinterpret_cast<const float4*>(W + 2 * TY + 4 * lane);
+        else if (y == g.ny - 1) pre.yf = *reinterpret_cast<const float4*>(W + 2 * TY + kTX + 4 * lane);
+      }
+      boundary_cells<true, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3, WRAP ? &pre : nullptr);
       float v[4];
       v[0] = hs_update(g.k, c.x, w0, e0, n.x, s.x, b.x, t.x, cs.x);
       v[1] = hs_update(g.k, c.y, c.x, e1, n.y, s.y, b.y, t.y, cs.y);
