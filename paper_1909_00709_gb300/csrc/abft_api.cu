@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -62,11 +63,15 @@ bool is_shallow(const abft_options& o, const abft_grid& G) { return o.shallow &&
 // boundaries
 bool general_opts(const abft_options& o) { return o.stencils != nullptr || o.boundary == ABFT_BC_CONST; }
 
-// rows per tile: streaming tiles default to 16, whole-column tiles to 8 (16 allowed); the
-// general kernels' tiles have kGenTY rows
-int pick_ty(const abft_options& o, const abft_grid& G) {
+// rows per tile: streaming tiles default to 16, whole-column tiles to 8 (16 allowed; 7 by
+// default where it balances a single grid's tiles over the SMs); the general kernels'
+// tiles have kGenTY rows
+int pick_ty(const abft_options& o, const abft_grid& G, int n_grids) {
   if (general_opts(o)) return kGenTY;
-  if (is_shallow(o, G)) return o.tile_y == 16 && G.nz <= 8 ? 16 : 8;
+  if (is_shallow(o, G)) {
+    if (o.tile_y == 16 && G.nz <= 8) return 16;
+    return o.tile_y == 0 && n_grids == 1 ? abft::balanced_shallow_rows(G) : 8;
+  }
   return o.tile_y == 8 || o.tile_y == 16 || o.tile_y == 32 ? o.tile_y : 16;
 }
 
@@ -94,7 +99,7 @@ bool make_plan(const abft_grid* grids, int n, const abft_options& o, Plan* P) {
   for (int i = 0; i < n; ++i) {
     const abft_grid& G = grids[i];
     if (!valid_grid(G)) return false;
-    const int ty = pick_ty(o, G);
+    const int ty = pick_ty(o, G, n);
     const size_t px = align_up(G.nx, 32);
     const size_t vol = px * G.ny * G.nz * sizeof(float);
     const size_t na = (size_t)G.nz * G.nx * 8, nb = (size_t)G.nz * G.ny * 8;
@@ -196,6 +201,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 namespace abft {
+
+// SMs of the current device (GB300's count where none can be asked, so that layouts
+// computed without a GPU are the same)
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, n = 0;
+    sms = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0
+              ? n
+              : 152;
+  }
+  return sms;
+}
+
+// Whole-column tiles of a grid swept alone: 8 rows, or 7 where that puts fewer rows on
+// the busiest SM.  A sweep ends when its slowest SM does, and two tiles share an SM once
+// there are more tiles than SMs: 512 rows in columns of 128 make 256 tiles of 8 rows, two
+// on 104 of 152 SMs, or 296 tiles of 7 rows, two on 144 SMs and each an eighth smaller.
+// Kept to at most two tiles per SM (the persistent kernels hold one tile per CTA).
+int balanced_shallow_rows(const abft_grid& G) {
+  const int64_t sms = device_sms(), ntx = (G.nx + kTX - 1) / kTX;
+  auto rows_on_busiest = [&](int ty) -> int64_t {
+    const int64_t tiles = ntx * ((G.ny + ty - 1) / ty);
+    return tiles > 2 * sms ? INT64_MAX : ty * ((tiles + sms - 1) / sms);
+  };
+  return rows_on_busiest(7) < rows_on_busiest(8) ? 7 : 8;
+}
 
 cudaError_t make_tensor_maps(const GridDev& g, int ty, CUtensorMap tm_u[3], CUtensorMap* tm_c, char* err,
                              size_t errlen) {
@@ -1431,7 +1464,7 @@ abft_status abft_init(abft_ctx** out, const abft_grid* grids, int32_t n_grids, c
     memset(&g, 0, sizeof g);
     g.nx = G.nx; g.ny = G.ny; g.nz = G.nz;
     g.px = (int)align_up(G.nx, 32);
-    g.ty = pick_ty(*opt, G);
+    g.ty = pick_ty(*opt, G, n_grids);
     g.shallow = is_shallow(*opt, G) ? 1 : 0;
     g.track = opt->track_residual;
     g.ntx = (G.nx + kTX - 1) / kTX;

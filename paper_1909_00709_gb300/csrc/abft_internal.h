@@ -17,6 +17,8 @@ constexpr int kFCap = 64;         // failing entries kept per plane and vector
 constexpr int kLocalFlips = 32;   // flips a tile can apply in one sweep
 constexpr int kSchedSteps = 4096; // sweeps covered by one uploaded schedule chunk
 constexpr int kShallowMaxZ = 16;  // grids this shallow are swept with whole-column tiles
+// rows of the whole-column tiles of a grid swept alone with the default tile height (7 or 8)
+int balanced_shallow_rows(const abft_grid& G);
 constexpr unsigned kSpinLimit = 1u << 26;  // bound of every device-side mbarrier wait loop
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // grid barrier wait bound
 constexpr unsigned long long kWaitTimeoutNs = 4ull * 1000 * 1000 * 1000;     // mbarrier wait bound

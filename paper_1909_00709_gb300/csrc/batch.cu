@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(256, 2)
 // ------------------------------------------------------------------ host side
 
 int batch_sweep_smem(int shallow, int ty, int nz) {
-  if (shallow) return ty == 16 ? ShallowTiles<16>::smem_bytes(nz) : ShallowTiles<8>::smem_bytes(nz);
+  if (shallow)
+    return ty == 16 ? ShallowTiles<16>::smem_bytes(nz)
+                    : (ty == 7 ? ShallowTiles<7>::smem_bytes(nz) : ShallowTiles<8>::smem_bytes(nz));
   switch (ty) {
     case 8: return StreamTiles<8>::smem_bytes(nz);
     case 32: return StreamTiles<32>::smem_bytes(nz);
@@ -207,6 +209,7 @@ static cudaError_t dispatch_bc(bool prep, const Launch* L, const BatchArgs* a, i
   if (shallow) {
     if (ty == 16) return dispatch_acc<ShallowTiles<16, BC>>(prep, L, a, blocks, smem, prot, acc);
     if (ty == 8) return dispatch_acc<ShallowTiles<8, BC>>(prep, L, a, blocks, smem, prot, acc);
+    if (ty == 7) return dispatch_acc<ShallowTiles<7, BC>>(prep, L, a, blocks, smem, prot, acc);
     return cudaErrorInvalidValue;
   }
   switch (ty) {

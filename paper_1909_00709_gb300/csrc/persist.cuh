@@ -514,7 +514,9 @@ static bool offline_fits_t(const GridDev& g) {
 template <int BC>
 static bool persistent_fits_cl(const GridDev& g, bool prot) {
   if (g.shallow)
-    return g.ty == 8 ? fits_t<ShallowTiles<8, BC>, 8>(g, prot) : fits_t<ShallowTiles<16, BC>, 16>(g, prot);
+    return g.ty == 7   ? fits_t<ShallowTiles<7, BC>, 7>(g, prot)
+           : g.ty == 8 ? fits_t<ShallowTiles<8, BC>, 8>(g, prot)
+                       : fits_t<ShallowTiles<16, BC>, 16>(g, prot);
   switch (g.ty) {
     case 8: return fits_t<StreamTiles<8, BC>, 8>(g, prot);
     case 16: return fits_t<StreamTiles<16, BC>, 16>(g, prot);
@@ -527,6 +529,7 @@ static cudaError_t launch_persistent_cl(const Launch& L, const PersistArgs& a, b
   const GridDev& g = a.g;
   if (g.shallow) {
     switch (g.ty) {
+      case 7: return launch_persist_ty<ShallowTiles<7, BC>, 7>(L, a, prot, blocks);
       case 8: return launch_persist_ty<ShallowTiles<8, BC>, 8>(L, a, prot, blocks);
       case 16: return launch_persist_ty<ShallowTiles<16, BC>, 16>(L, a, prot, blocks);
       default: return cudaErrorInvalidValue;
@@ -545,6 +548,7 @@ static cudaError_t launch_offline_cl(const Launch& L, const PersistArgs& a, int*
   const GridDev& g = a.g;
   if (g.shallow) {
     switch (g.ty) {
+      case 7: return launch_offline_ty<ShallowTiles<7, BC>, 7>(L, a, blocks);
       case 8: return launch_offline_ty<ShallowTiles<8, BC>, 8>(L, a, blocks);
       case 16: return launch_offline_ty<ShallowTiles<16, BC>, 16>(L, a, blocks);
       default: return cudaErrorInvalidValue;
@@ -560,7 +564,10 @@ static cudaError_t launch_offline_cl(const Launch& L, const PersistArgs& a, int*
 
 template <int BC>
 static bool offline_fits_cl(const GridDev& g) {
-  if (g.shallow) return g.ty == 8 ? offline_fits_t<ShallowTiles<8, BC>, 8>(g) : offline_fits_t<ShallowTiles<16, BC>, 16>(g);
+  if (g.shallow)
+    return g.ty == 7   ? offline_fits_t<ShallowTiles<7, BC>, 7>(g)
+           : g.ty == 8 ? offline_fits_t<ShallowTiles<8, BC>, 8>(g)
+                       : offline_fits_t<ShallowTiles<16, BC>, 16>(g);
   switch (g.ty) {
     case 8: return offline_fits_t<StreamTiles<8, BC>, 8>(g);
     case 16: return offline_fits_t<StreamTiles<16, BC>, 16>(g);

@@ -181,6 +181,7 @@ static cudaError_t launch_sweep_bc(const Launch& L, const GridDev& g, const CUte
                                    const CUtensorMap& tm_c, int in, int out, bool prot) {
   if (g.shallow) {
     switch (g.ty) {
+      case 7: return launch_tiles<ShallowTiles<7, BC>>(L, g, tm_in, tm_c, in, out, prot);
       case 8: return launch_tiles<ShallowTiles<8, BC>>(L, g, tm_in, tm_c, in, out, prot);
       case 16: return launch_tiles<ShallowTiles<16, BC>>(L, g, tm_in, tm_c, in, out, prot);
       default: return cudaErrorInvalidValue;
@@ -222,6 +223,7 @@ static cudaError_t launch_redo_bc(const Launch& L, const GridDev& g, const CUten
                                   const CUtensorMap& tm_c, int in, int out) {
   if (g.shallow) {
     switch (g.ty) {
+      case 7: return redo_t<ShallowTiles<7, BC>, 7>(L, g, tm_in, tm_c, in, out);
       case 8: return redo_t<ShallowTiles<8, BC>, 8>(L, g, tm_in, tm_c, in, out);
       case 16: return redo_t<ShallowTiles<16, BC>, 16>(L, g, tm_in, tm_c, in, out);
       default: return cudaErrorInvalidValue;

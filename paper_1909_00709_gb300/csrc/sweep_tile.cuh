@@ -700,10 +700,16 @@ __device__ __forceinline__ void shallow_tile_issue(const CUtensorMap* tm_u, cons
 
 // Periodic boundaries on whole-column tiles: the wrapped values of the rows of plane z
 // that this lane needs -- u at x = nx - 1 for a row's first point (W[r]), at x = 0 for
-// its last (W[TY + r]), and on a y face the row on the other face (W + 2 TY: for y = 0;
-// W + 2 TY + kTX: for y = ny - 1) -- copied from global memory to the plane's slice W of
-// a shared buffer.  Called before the wait for the tile's copy, so that these loads run
-// while it is in flight; a lane later reads only what it wrote.
+// its last (W[TY + r]), and on a y face the row on the other face (W + WrapCols<TY>::X:
+// for y = 0; W + X + kTX: for y = ny - 1) -- copied from global memory to the plane's
+// slice W of a shared buffer.  Called before the wait for the tile's copy, so that these
+// loads run while it is in flight; a lane later reads only what it wrote.
+template <int TY>
+struct WrapCols {
+  static constexpr int X = (2 * TY + 3) / 4 * 4;  // the row copies start 16-byte aligned
+  static constexpr int PLANE = X + 2 * kTX;       // floats per plane (a multiple of 4)
+};
+
 template <int TY>
 __device__ __forceinline__ void wrap_fetch(const GridDev& g, const float* __restrict__ uin, int z, int y0, int gx0,
                                            int last, int lane, float* W) {
@@ -727,8 +733,9 @@ __device__ __forceinline__ void wrap_fetch(const GridDev& g, const float* __rest
     if (gx0 == 0) W[r] = xw[r];
     if (last <= 3) W[TY + r] = xe[r];
   }
-  if (y0 == 0) *reinterpret_cast<float4*>(W + 2 * TY + 4 * lane) = yn;
-  if (y0 + TY >= g.ny) *reinterpret_cast<float4*>(W + 2 * TY + kTX + 4 * lane) = ys;
+  constexpr int X = WrapCols<TY>::X;
+  if (y0 == 0) *reinterpret_cast<float4*>(W + X + 4 * lane) = yn;
+  if (y0 + TY >= g.ny) *reinterpret_cast<float4*>(W + X + kTX + 4 * lane) = ys;
 }
 
 template <int TY, bool PROT, int ACC, int BC, int VEC = 2>
@@ -744,7 +751,7 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
   const int last = g.nx - 1 - gx0;
   // periodic: this warp's planes' wrapped values, fetched while the tile's copy is in flight
   constexpr bool WRAP = BC == ABFT_BC_PERIODIC;
-  constexpr int WPL = 2 * TY + 2 * kTX;  // floats of wrapped values per plane
+  constexpr int WPL = WrapCols<TY>::PLANE;  // floats of wrapped values per plane
   __shared__ __align__(16) float wbuf[WRAP ? kShallowMaxZ * WPL : 4];
   if (WRAP)
     for (int z = warp; z < nz; z += NW) wrap_fetch<TY>(g, uin, z, y0, gx0, last, lane, wbuf + z * WPL);
@@ -766,7 +773,11 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
     const float* Cz = sm.c + z * TY * kTX;
     AccA<ACC> acc;
     if (PA_ON) acc.zero();
-    typename RowPart<ACC>::T rp[TY];
+    // row partials, padded with empty rows to a power of two for reduce_rows
+    constexpr int RP = TY <= 8 ? 8 : 16;
+    typename RowPart<ACC>::T rp[RP];
+#pragma unroll
+    for (int r = TY; r < RP; ++r) rp[r] = typename RowPart<ACC>::T{};
 #pragma unroll
     for (int r = 0; r < TY; ++r) {
       const int y = y0 + r;
@@ -787,8 +798,8 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
       if (WRAP && y < g.ny && last >= 0) {
         pre.xw = W[r];
         pre.xe = W[TY + r];
-        if (y == 0) pre.yf = *reinterpret_cast<const float4*>(W + 2 * TY + 4 * lane);
-        else if (y == g.ny - 1) pre.yf = *reinterpret_cast<const float4*>(W + 2 * TY + kTX + 4 * lane);
+        if (y == 0) pre.yf = *reinterpret_cast<const float4*>(W + WrapCols<TY>::X + 4 * lane);
+        else if (y == g.ny - 1) pre.yf = *reinterpret_cast<const float4*>(W + WrapCols<TY>::X + kTX + 4 * lane);
       }
       boundary_cells<true, BC>(g, uin, z, y, gx0, last, c, n, s, b, t, w0, e0, e1, e2, e3, WRAP ? &pre : nullptr);
       float v[4];
@@ -828,10 +839,11 @@ __device__ __forceinline__ void shallow_tile_run(const GridDev& g, const float* 
     }
     if (PROT) {
       if (PA_ON) acc.store4(PA, ((size_t)tyi * nz + z) * g.pa_stride + gx0);
-      const typename RowPart<ACC>::T tot = reduce_rows<ACC, TY>(rp, lane);
-      constexpr int SH = TY == 8 ? 2 : 1;  // lane l holds row l >> SH
+      const typename RowPart<ACC>::T tot = reduce_rows<ACC, RP>(rp, lane);
+      constexpr int SH = RP == 8 ? 2 : 1;  // lane l holds row l >> SH
       const int r = lane >> SH, y = y0 + r;
-      if ((lane & ((1 << SH) - 1)) == 0 && y < g.ny) RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.pb_stride + y, tot);
+      if ((lane & ((1 << SH) - 1)) == 0 && r < TY && y < g.ny)
+        RowPart<ACC>::store(PB, ((size_t)txi * nz + z) * g.pb_stride + y, tot);
     }
   }
   fence_proxy_async_global();

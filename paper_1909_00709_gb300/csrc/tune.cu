@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "abft.h"
+#include "abft_internal.h"
 
 namespace {
 
@@ -54,8 +55,9 @@ std::string effect_of(const abft_grid* g, int n, const Cand& c, int mode, int bc
   std::string e;
   char b[32];
   for (int i = 0; i < n; ++i) {
-    const bool sh = c.shallow && g[i].nz <= 16;
-    const int ty = sh ? (c.tile_y == 16 && g[i].nz <= 8 ? 16 : 8) : c.tile_y;
+    const bool sh = c.shallow && g[i].nz <= abft::kShallowMaxZ;
+    const int auto_rows = c.tile_y == 0 && n == 1 ? abft::balanced_shallow_rows(g[i]) : 8;
+    const int ty = sh ? (c.tile_y == 16 && g[i].nz <= 8 ? 16 : auto_rows) : (c.tile_y == 0 ? 16 : c.tile_y);
     snprintf(b, sizeof b, "%d%d;", sh ? 1 : 0, ty);
     e += b;
   }
@@ -73,7 +75,7 @@ std::vector<Cand> candidates(const abft_grid* g, int n, int mode, int bc, int ac
     for (int batch : {1, 0})
       for (int persistent : {1, 0})
         for (int shallow : {1, 0})
-          for (int ty : {8, 16, 32}) {
+          for (int ty : {0, 8, 16, 32}) {  // 0: the library's default height
             const Cand c{ty, shallow, persistent, batch, depth};
             const std::string e = effect_of(g, n, c, mode, bc, acc);
             if (std::find(seen.begin(), seen.end(), e) != seen.end()) continue;
