@@ -45,7 +45,7 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) per sweep of the dominant kernel, from one ncu capture of
 # the current build (the working set stays in L2); None for kernels not captured since
 # they last changed
-TRAFFIC_PER_SWEEP = {}  # the whole-column tiles of 7 rows have not been captured yet
+TRAFFIC_PER_SWEEP = {"k_persist_online": (16982016 + 127232) / 1000}  # one 1000-sweep launch, 512x512x8
 PRECISION_SHAPE = (512, 512, 64)
 PRECISION_SWEEPS = 500
 LARGE_SHAPE = (1024, 1024, 256)
