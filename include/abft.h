@@ -115,7 +115,10 @@ typedef struct {
   int32_t acc;              /* abft_acc */
   int32_t event_capacity;   /* events kept on the device (>= 1) */
   int32_t graph_steps;      /* sweeps per captured CUDA graph; 0 disables graphs */
-  int32_t tile_y;           /* rows per sweep tile (8, 16 or 32); 0 = library default */
+  int32_t tile_y;           /* rows per sweep tile (8, 16 or 32); 0 = library default: 16 for
+                               streaming tiles, 8 for whole-column tiles, or 7 in a context of
+                               one grid where 7-row tiles put fewer rows on the busiest SM (a
+                               sweep ends when its slowest SM does); the tuner may return 0 */
   int32_t max_flips_per_step; /* schedule capacity per step and grid (<= 511) */
   int32_t persistent;       /* 1: run online/unprotected sweeps in one persistent cooperative
                                launch per grid and schedule chunk where the grid's tiles fit one per
