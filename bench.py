@@ -650,8 +650,8 @@ def side_runs(dev, stream, flush, hbm_peak):
     # general stencil sets (Sec. 3.1) and the constant boundary (Sec. 3.3) through the
     # general kernels, 1024x1024x64
     gshape = (1024, 1024, 64)
-    star = [(0, 0, 0, 0.5)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
-           [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)]
+    star = [(0, 0, 0, 0.25)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
+           [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)] + [(0, 0, d, 0.0625) for d in (-2, -1, 1, 2)]
     box = [(i, j, k, 1.0 / 27) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1)]
     gen = {}
     for gname, kw in (("star13_clamped", dict(stencils=[star])), ("box27_clamped", dict(stencils=[box])),
@@ -760,7 +760,7 @@ def side_runs(dev, stream, flush, hbm_peak):
                                   "checksum vector, passes of `depth` sweeps, every level checked, a failed pass "
                                   "recomputed sweep by sweep"},
             "general_stencils": {"shape": list(gshape), "sweeps": 40, "glups": gen,
-                                 "sets": {"star13": "centre 1/2, x and y offsets +-1, +-2 at 1/16",
+                                 "sets": {"star13": "centre 1/4, x, y and z offsets +-1, +-2 at 1/16",
                                           "box27": "27-point box, 1/27 each"}},
             "boundaries": {"glups": bnd, "mode": "fault-free", "offline_delta": 16},
             "one_vector": {"glups": onev, "mode": "online; *_flips at the stated rate"}, "batch": batch,
@@ -827,8 +827,8 @@ def run_profile_case(args):
             c.step(8, abi.MODE_NONE)
             launches += c.counters()["kernel_launches"]
     elif args.case == "general":  # a 13-point star: online with flips, then offline windows
-        star = [(0, 0, 0, 0.5)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
-               [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)] + [(0, 0, d, 0.0) for d in (-1, 1)]
+        star = [(0, 0, 0, 0.25)] + [(d, 0, 0, 0.0625) for d in (-2, -1, 1, 2)] + \
+               [(0, d, 0, 0.0625) for d in (-2, -1, 1, 2)] + [(0, 0, d, 0.0625) for d in (-2, -1, 1, 2)]
         with ctx([big], [4], stencils=[star]) as c:
             c.inject(4, 2.0, 0xFFFFFFFF)
             c.step(6, abi.MODE_ONLINE)
