@@ -158,3 +158,23 @@ def test_schedule_rejects_bad_arguments(abi):
 def test_status_strings(abi):
     assert abi.abft_status_string(0) == "ok"
     assert "timed out" in abi.abft_status_string(5)
+
+
+def test_whole_column_tile_height_follows_the_sm_balance(abi):
+    """A grid swept alone on whole-column tiles gets 7-row tiles by default where that
+    puts fewer rows on the busiest of the GPU's 152 SMs, which shows in the workspace:
+    more tile rows mean larger tile-row partial buffers (two sets of nz x ntx x 128 FP32
+    values per tile row).  An explicit tile_y = 8, a grid where 7 rows would not balance
+    better, and a context of several grids keep 8 rows."""
+    d, e8 = abi.abft_default_options(), abi.abft_default_options(tile_y=8)
+    # 512 rows: 74 tile rows of 7 against 64 of 8 (296 tiles against 256)
+    extra = abi.abft_workspace_bytes([(512, 512, 8)], d) - abi.abft_workspace_bytes([(512, 512, 8)], e8)
+    per_tile_row = 2 * 8 * 4 * 128 * 4  # two partial sets, nz = 8, ntx = 4
+    assert 10 * per_tile_row <= extra < 10 * per_tile_row + 4096
+    # 608 rows: 87 tile rows of 7 would put more than two tiles on some SMs
+    assert abi.abft_workspace_bytes([(512, 608, 8)], d) == abi.abft_workspace_bytes([(512, 608, 8)], e8)
+    # a batch keeps 8 rows; deep grids use streaming tiles of 16 rows by default
+    pair = [(512, 512, 8), (64, 64, 8)]
+    assert abi.abft_workspace_bytes(pair, d) == abi.abft_workspace_bytes(pair, e8)
+    assert abi.abft_workspace_bytes([(512, 512, 64)], d) == \
+        abi.abft_workspace_bytes([(512, 512, 64)], abi.abft_default_options(tile_y=16))
